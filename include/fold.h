@@ -1,0 +1,155 @@
+/*
+ * fold.h -- C-ABI of libfold_b300: B300-native (sm_103a) Nussinov RNA folding
+ * with the two-vector Four-Russians speedup of Venkatachalam, Gusfield and
+ * Frid, "Faster Algorithms for RNA-folding using the Four-Russians method".
+ *
+ * What is computed (Section 2, Eq. 1).  For a sequence S of n bases the
+ * library fills the table D(i,j), 0 <= i <= j < n, of the maximum number of
+ * disjoint, non-crossing complementary base pairs inside S[i..j]:
+ *     D(i,i) = D(i+1,i) = 0,
+ *     D(i,j) = max( b(S_i,S_j) + D(i+1,j-1),  max_{i<k<=j} D(i,k-1) + D(k,j) ),
+ * and the answer ("max pairs") D(0,n-1).  The default method evaluates the
+ * second line with the two-vector scheme of Section 3.1: a table R over all
+ * pairs of (q-1)-bit row/column difference vectors (built once by fold_init)
+ * turns every group of q consecutive splits into one lookup (Eq. 3); splits
+ * outside full groups are evaluated directly.  The plain method (kept as the
+ * comparison) evaluates every split directly.  Both produce identical D.
+ *
+ * Conventions shared by every entry point:
+ *   - positions are 0-based; bases are 'A','C','G','U' in either case, coded
+ *     A=0, C=1, G=2, U=3; anything else is rejected with FOLD_EINVAL;
+ *   - pair_mask bit (4*x + y) set means b(x,y) = 1, x being the base at the
+ *     smaller position (asymmetric masks are allowed);
+ *     FOLD_PAIRS_DEFAULT = {AU,UA,CG,GC,GU,UG}, FOLD_PAIRS_PAPER = {AU,UA,CG,GC};
+ *   - no minimum hairpin loop: D(i,i+1) = b(S_i,S_{i+1});
+ *   - 0 <= n <= FOLD_MAX_N; D values fit int16 (D <= n/2);
+ *   - D tables handed back are n*n int16 row-major, D_out[i*n+j] = D(i,j) for
+ *     i <= j and 0 for i > j;
+ *   - every call returns a status code; no exception crosses the ABI;
+ *   - the context owns its device state; the caller owns every buffer it
+ *     passes, and inputs are not retained after a call returns (serve_submit
+ *     copies the sequence);
+ *   - a context is used by one thread at a time, except fold_serve_submit and
+ *     fold_serve_poll, which are thread-safe.
+ */
+#ifndef FOLD_B300_H
+#define FOLD_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FOLD_ABI_VERSION 1
+#define FOLD_MAX_N 65535
+#define FOLD_PAIRS_DEFAULT ((uint16_t)0x5A48)
+#define FOLD_PAIRS_PAPER ((uint16_t)0x1248)
+
+typedef struct fold_ctx fold_ctx;
+
+enum fold_status {
+    FOLD_OK = 0,
+    FOLD_EINVAL = 1,    /* bad argument: q, mask, base letter, length, NULL pointer, size */
+    FOLD_ENOMEM = 2,    /* device or host allocation failed, or workspace too small */
+    FOLD_EAGAIN = 3,    /* serving: over the memory budget or the in-flight limit; retry later */
+    FOLD_ETIMEOUT = 4,  /* a bounded device-side wait expired; results are not valid */
+    FOLD_ECUDA = 5,     /* a CUDA runtime call failed */
+    FOLD_ENOTREADY = 6  /* serving: the ticket is still in flight */
+};
+
+enum fold_method {
+    FOLD_METHOD_TWO_VECTOR = 0, /* Section 3.1 / Section 4: R-table lookups per group of q splits */
+    FOLD_METHOD_PLAIN = 1       /* Section 2 / Section 4: every split evaluated (comparison kernel) */
+};
+
+enum fold_option {
+    FOLD_OPT_METHOD = 1,      /* fold_method; default FOLD_METHOD_TWO_VECTOR */
+    FOLD_OPT_GRID = 2,        /* persistent CTAs; 0 = one wave (SM count x resident CTAs/SM) */
+    FOLD_OPT_TIMEOUT_MS = 3,  /* bound on every device-side wait; default 5000 */
+    FOLD_OPT_KCHUNK = 4,      /* middle tile columns per FAR chunk; 0 = automatic */
+    FOLD_OPT_Q = 5,           /* read-only: q in use */
+    FOLD_OPT_TILE = 6,        /* read-only: tile edge T of the current method */
+    FOLD_OPT_LAUNCHES = 7,    /* read-only: kernels launched by this context so far */
+    FOLD_OPT_TEST_DROP_TASK = 8 /* fault injection for tests: 1 = leave the tile (0,1) task out of the
+                                   next single-sequence schedules, so its dependents' bounded waits
+                                   expire and the call returns FOLD_ETIMEOUT; 0 = off (default) */
+};
+
+/* Creates a context on `device`.  q in [2,10] is the vector length of
+ * Section 3.1 (0 picks the default, 8); pair_mask as above (must be non-zero
+ * only on bits for codes 0..3).  Builds the R table (2^(2(q-1)) entries,
+ * Section 3.1 preprocessing) on the device.  On success *out owns the context
+ * (free with fold_destroy).  Errors: FOLD_EINVAL, FOLD_ECUDA, FOLD_ENOMEM. */
+int fold_init(int q, uint16_t pair_mask, int device, fold_ctx **out);
+
+/* Stops serving if active and releases every resource of the context. */
+void fold_destroy(fold_ctx *ctx);
+
+/* Static, human-readable text for a status code. */
+const char *fold_strerror(int code);
+
+/* Sets / reads an option (enum fold_option).  FOLD_EINVAL on an unknown
+ * option or out-of-range value. */
+int fold_set_option(fold_ctx *ctx, int option, int64_t value);
+int fold_get_option(fold_ctx *ctx, int option, int64_t *value);
+
+/* Copies the R table to host memory: out[(h << (q-1)) | c] = R(h,c) for the
+ * (q-1)-bit horizontal vector h and vertical vector c (bit p-1 holds
+ * difference p; vertical differences stored as positive bits).  cap is the
+ * size of out in bytes and must be >= 4^(q-1).  Section 3.1. */
+int fold_rtable(fold_ctx *ctx, uint8_t *out, int64_t cap);
+
+/* Folds one sequence from host memory (synchronous).  seq: n letters;
+ * max_pairs (non-NULL) receives D(0,n-1) (0 for n <= 1); D_out (nullable)
+ * receives the n*n table.  Device memory is managed by the context. */
+int fold_score(fold_ctx *ctx, const char *seq, int32_t n, int32_t *max_pairs, int16_t *D_out);
+
+/* Device-resident path for callers that own device memory (e.g. PyTorch).
+ * fold_workspace_bytes returns the workspace size needed for length n (or a
+ * negative status).  fold_score_dev enqueues the fold on `stream` (a
+ * cudaStream_t; NULL is the CUDA default stream, as in the CUDA runtime API)
+ * and returns without waiting:
+ *   d_codes    n device bytes with codes 0..3 (not validated on the device);
+ *   d_ws       device workspace of ws_bytes >= fold_workspace_bytes(ctx, n),
+ *              256-byte aligned, owned by the caller, not reused until the
+ *              stream has passed this call;
+ *   d_max_pairs one device int32: D(0,n-1), or -FOLD_ETIMEOUT if a
+ *              device-side wait expired;
+ *   d_D_out    nullable device buffer of n*n int16 for the full table.
+ * Inside the workspace D is kept twice as int16 (row-major and column-major,
+ * padded to a multiple of the tile edge), plus the packed difference vectors
+ * and the tile flags of the persistent kernel. */
+int64_t fold_workspace_bytes(fold_ctx *ctx, int32_t n);
+int fold_score_dev(fold_ctx *ctx, const uint8_t *d_codes, int32_t n, void *d_ws, int64_t ws_bytes,
+                   int32_t *d_max_pairs, int16_t *d_D_out, void *stream);
+
+/* Folds `count` sequences in one persistent launch (sequence-level and
+ * wavefront parallelism together).  seqs[k] has lens[k] letters;
+ * max_pairs_out[k] receives D_k(0,n_k-1); D_out may be NULL, and so may any
+ * D_out[k] (else lens[k]*lens[k] int16).  Synchronous. */
+int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int32_t *lens,
+               int32_t *max_pairs_out, int16_t *const *D_out);
+
+/* Serving (continuous batching).  fold_serve_start starts a host scheduler
+ * thread that admits submitted requests while the device memory their two
+ * int16 D copies need (about 4*n^2 bytes each) fits `budget_bytes` and at
+ * most `max_inflight` are in flight, and folds the admitted set in repeated
+ * persistent launches, each advancing every in-flight request by a slice of
+ * tile diagonals; requests that arrive while others are on the GPU join at
+ * the next slice.  fold_serve_submit copies the sequence and returns a ticket
+ * (FOLD_EAGAIN if the request alone exceeds the budget or the queue is
+ * full).  fold_serve_poll returns FOLD_ENOTREADY while in flight and FOLD_OK
+ * once done, filling max_pairs (and D_out, n*n int16, if not NULL); the ticket
+ * is then released.  fold_serve_stop drains nothing: in-flight requests are
+ * abandoned and their tickets become invalid. */
+int fold_serve_start(fold_ctx *ctx, int64_t budget_bytes, int32_t max_inflight);
+int fold_serve_submit(fold_ctx *ctx, const char *seq, int32_t n, uint64_t *ticket);
+int fold_serve_poll(fold_ctx *ctx, uint64_t ticket, int32_t *max_pairs, int16_t *D_out);
+int fold_serve_stop(fold_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FOLD_B300_H */

@@ -1,0 +1,471 @@
+// api.cu -- C-ABI of libfold_b300 (declared in include/fold.h): context,
+// workspace planning, single and batched folds.  Serving lives in serve.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/fold.h"
+#include "api_internal.h"
+#include "fold_common.h"
+#include "kernels.h"
+#include "schedule.h"
+
+using namespace fold;
+
+namespace fold {
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int kc_auto(int NT) { return std::min(64, std::max(4, NT / 24)); }
+
+// Layout of `count` sequences inside one workspace.  Sections (256-byte
+// aligned): control | results | flags | counters | P ring | codes | Drow |
+// Dcol | row features | column features.  The first five are zeroed before
+// every launch.
+Plan make_plan(const int32_t *lens, int count, int q, int method) {
+    Plan pl;
+    pl.q = q;
+    pl.method = method;
+    pl.T = tile_of(q, method);
+    pl.count = count;
+    const int T = pl.T;
+    size_t o_code = 0, o_drow = 0, o_dcol = 0, o_rf = 0, o_cf = 0, o_flag = 0, o_cnt = 0, o_p = 0;
+    pl.sd.resize(count);
+    pl.NTs.resize(count);
+    for (int k = 0; k < count; ++k) {
+        SeqDesc &d = pl.sd[k];
+        memset(&d, 0, sizeof d);
+        int n = lens[k];
+        int NT = n > 0 ? (n + T - 1) / T : 0;
+        int Np = NT * T;
+        d.n = n;
+        d.NT = NT;
+        d.Np = Np;
+        d.PC = round_up(Np + kColOff + 1, 8);
+        d.result_index = k;
+        d.code_off = (long long)o_code;  o_code += align_up((size_t)Np, 128);
+        d.drow_off = (long long)o_drow;  o_drow += align_up((size_t)Np * Np, 64);
+        d.dcol_off = (long long)o_dcol;  o_dcol += align_up((size_t)Np * d.PC, 64);
+        if (method == kTwoVector) {
+            d.rf_off = (long long)o_rf;  o_rf += align_up((size_t)Np * (Np / q), 32);
+            d.cf_off = (long long)o_cf;  o_cf += align_up((size_t)(Np / q) * Np, 32);
+        }
+        d.flag_off = (long long)o_flag; o_flag += align_up((size_t)NT * NT, 32);
+        d.cnt_off = (long long)o_cnt;   o_cnt += align_up((size_t)NT * NT, 32);
+        d.p_off = (long long)o_p;       o_p += (size_t)kRing * NT * T * T;
+        pl.NTs[k] = NT;
+    }
+    size_t off = 0;
+    pl.off_control = off; off = align_up(off + 256, 256);
+    pl.off_results = off; off = align_up(off + 4 * (size_t)std::max(count, 1), 256);
+    pl.off_flags = off;   off = align_up(off + 4 * o_flag, 256);
+    pl.off_cnt = off;     off = align_up(off + 4 * o_cnt, 256);
+    pl.off_pring = off;   off = align_up(off + 4 * o_p, 256);
+    pl.zero_bytes = off;
+    pl.off_codes = off;   off = align_up(off + o_code, 256);
+    pl.off_drow = off;    off = align_up(off + 2 * o_drow, 256);
+    pl.off_dcol = off;    off = align_up(off + 2 * o_dcol, 256);
+    pl.off_rf = off;      off = align_up(off + 4 * o_rf, 256);
+    pl.off_cf = off;      off = align_up(off + 4 * o_cf, 256);
+    pl.bytes = off;
+    return pl;
+}
+
+FoldParams make_params(const fold_ctx *ctx, const Plan &pl, uint8_t *ws, const int4 *tasks, int ntasks,
+                       const SeqDesc *d_sd) {
+    FoldParams p;
+    memset(&p, 0, sizeof p);
+    p.tasks = tasks;
+    p.ntasks = ntasks;
+    p.queue_head = reinterpret_cast<int *>(ws + pl.off_control);
+    p.error = reinterpret_cast<int *>(ws + pl.off_control) + 1;
+    p.seqs = d_sd;
+    p.codes = ws + pl.off_codes;
+    p.drow = reinterpret_cast<int16_t *>(ws + pl.off_drow);
+    p.dcol = reinterpret_cast<int16_t *>(ws + pl.off_dcol);
+    p.rf = reinterpret_cast<uint32_t *>(ws + pl.off_rf);
+    p.cf = reinterpret_cast<uint32_t *>(ws + pl.off_cf);
+    p.flags = reinterpret_cast<int *>(ws + pl.off_flags);
+    p.cnt = reinterpret_cast<int *>(ws + pl.off_cnt);
+    p.pring = reinterpret_cast<int *>(ws + pl.off_pring);
+    p.results = reinterpret_cast<int *>(ws + pl.off_results);
+    p.rtab = ctx->d_rpacked;
+    p.pair64 = ctx->pair64;
+    p.timeout_ns = ctx->timeout_ms * 1000000LL;
+    return p;
+}
+
+int grid_for(fold_ctx *ctx) {
+    if (ctx->grid_override > 0) return ctx->grid_override;
+    int bps = fold_blocks_per_sm(ctx->q, ctx->method);
+    if (bps < 1) bps = 1;
+    return ctx->sm_count * bps;
+}
+
+int status_from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return FOLD_OK;
+    if (e == cudaErrorMemoryAllocation) return FOLD_ENOMEM;
+    return FOLD_ECUDA;
+}
+
+// device buffer that grows on demand (context-owned)
+int ensure_buf(DevBuf &b, size_t bytes) {
+    if (b.bytes >= bytes && b.ptr) return FOLD_OK;
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.ptr, std::max<size_t>(bytes, 256));
+    if (e != cudaSuccess) { cudaGetLastError(); return FOLD_ENOMEM; }
+    b.bytes = std::max<size_t>(bytes, 256);
+    return FOLD_OK;
+}
+
+int ensure_host(HostBuf &b, size_t bytes) {
+    if (b.bytes >= bytes && b.ptr) return FOLD_OK;
+    if (b.ptr) cudaFreeHost(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMallocHost(&b.ptr, std::max<size_t>(bytes, 256));
+    if (e != cudaSuccess) { cudaGetLastError(); return FOLD_ENOMEM; }
+    b.bytes = std::max<size_t>(bytes, 256);
+    return FOLD_OK;
+}
+
+// Base letters to codes; returns false on an invalid letter.
+bool encode_seq(const char *seq, int n, uint8_t *out) {
+    for (int k = 0; k < n; ++k) {
+        switch (seq[k]) {
+            case 'A': case 'a': out[k] = 0; break;
+            case 'C': case 'c': out[k] = 1; break;
+            case 'G': case 'g': out[k] = 2; break;
+            case 'U': case 'u': out[k] = 3; break;
+            default: return false;
+        }
+    }
+    return true;
+}
+
+// Cached device schedule + descriptor for a single sequence of length n.
+int single_schedule(fold_ctx *ctx, int n, const Plan &pl, const int4 **tasks, int *ntasks, const SeqDesc **d_sd) {
+    int NT = pl.NTs[0];
+    int kc = ctx->kc_override > 0 ? ctx->kc_override : kc_auto(NT);
+    long long key = ((long long)n << 24) | ((long long)ctx->method << 20) | ((long long)ctx->q << 16) | kc;
+    if (ctx->test_drop_task) key = -key - 1;   // separate cache entry for the fault-injection schedule
+    auto it = ctx->sched_cache.find(key);
+    if (it == ctx->sched_cache.end()) {
+        std::vector<int4> tv;
+        build_schedule(pl.NTs, kc, tv);
+        if (ctx->test_drop_task) {
+            // host-side fault injection: drop the NEAR task of tile (0,1)
+            for (size_t k = 0; k < tv.size(); ++k)
+                if (task_type(tv[k].y) == kTaskNear && task_I(tv[k].y) == 0 && task_J(tv[k].y) == 1) {
+                    tv.erase(tv.begin() + (long)k);
+                    break;
+                }
+        }
+        CachedSched cs;
+        cs.ntasks = (int)tv.size();
+        size_t bytes = tv.size() * sizeof(int4) + 256 + sizeof(SeqDesc);
+        if (cudaMalloc(&cs.dev, bytes) != cudaSuccess) { cudaGetLastError(); return FOLD_ENOMEM; }
+        cs.d_sd = reinterpret_cast<SeqDesc *>(cs.dev);
+        cs.d_tasks = reinterpret_cast<int4 *>(reinterpret_cast<uint8_t *>(cs.dev) + 256);
+        cudaError_t e = cudaMemcpy(cs.d_sd, pl.sd.data(), sizeof(SeqDesc), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !tv.empty())
+            e = cudaMemcpy(cs.d_tasks, tv.data(), tv.size() * sizeof(int4), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cudaFree(cs.dev); return status_from_cuda(e); }
+        it = ctx->sched_cache.emplace(key, cs).first;
+    }
+    *tasks = it->second.d_tasks;
+    *ntasks = it->second.ntasks;
+    *d_sd = it->second.d_sd;
+    return FOLD_OK;
+}
+
+// Enqueues the fold of one sequence whose codes are in device memory.
+int enqueue_single(fold_ctx *ctx, const uint8_t *d_codes, int n, uint8_t *ws, size_t ws_bytes, int32_t *d_out,
+                   int16_t *d_D, cudaStream_t st) {
+    int32_t len = n;
+    Plan pl = make_plan(&len, 1, ctx->q, ctx->method);
+    if (ws_bytes < pl.bytes) return FOLD_ENOMEM;
+    cudaError_t e = cudaMemsetAsync(ws, 0, pl.zero_bytes, st);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    if (n >= 1) {
+        const int4 *tasks;
+        int ntasks;
+        const SeqDesc *d_sd;
+        int rc = single_schedule(ctx, n, pl, &tasks, &ntasks, &d_sd);
+        if (rc) return rc;
+        e = launch_pad_codes(d_codes, n, pl.sd[0].Np, ws + pl.off_codes, st);
+        if (e != cudaSuccess) return status_from_cuda(e);
+        FoldParams p = make_params(ctx, pl, ws, tasks, ntasks, d_sd);
+        e = launch_fold(p, ctx->q, ctx->method, grid_for(ctx), st);
+        if (e != cudaSuccess) return status_from_cuda(e);
+        ctx->launches += 2;
+    }
+    e = launch_finalize(reinterpret_cast<int *>(ws + pl.off_control) + 1, reinterpret_cast<int *>(ws + pl.off_results),
+                        1, d_out, st);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    ctx->launches += 1;
+    if (d_D && n > 0) {
+        e = launch_extract(reinterpret_cast<int16_t *>(ws + pl.off_drow), pl.sd[0].Np, n, d_D, st);
+        if (e != cudaSuccess) return status_from_cuda(e);
+        ctx->launches += 1;
+    }
+    return FOLD_OK;
+}
+
+}  // namespace fold
+
+// ====================================================================== C-ABI
+extern "C" {
+
+const char *fold_strerror(int code) {
+    switch (code) {
+        case FOLD_OK: return "ok";
+        case FOLD_EINVAL: return "invalid argument";
+        case FOLD_ENOMEM: return "out of memory (device, host, or workspace too small)";
+        case FOLD_EAGAIN: return "resource temporarily unavailable (serving budget or queue)";
+        case FOLD_ETIMEOUT: return "device-side wait timed out";
+        case FOLD_ECUDA: return "CUDA runtime error";
+        case FOLD_ENOTREADY: return "request still in flight";
+    }
+    return "unknown status";
+}
+
+int fold_init(int q, uint16_t pair_mask, int device, fold_ctx **out) {
+    if (!out) return FOLD_EINVAL;
+    *out = nullptr;
+    if (q == 0) q = 8;
+    if (q < 2 || q > 10) return FOLD_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return device < 0 ? FOLD_EINVAL : FOLD_ECUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return FOLD_ECUDA;
+    fold_ctx *ctx = new (std::nothrow) fold_ctx();
+    if (!ctx) return FOLD_ENOMEM;
+    ctx->device = device;
+    ctx->q = q;
+    ctx->pair_mask = pair_mask;
+    ctx->pair64 = 0;
+    for (int x = 0; x < 4; ++x)
+        for (int y = 0; y < 4; ++y)
+            if ((pair_mask >> (4 * x + y)) & 1) ctx->pair64 |= 1ULL << (8 * x + y);
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete ctx;
+        return FOLD_ECUDA;
+    }
+    size_t nent = (size_t)1 << (2 * (q - 1));
+    // both copies padded to 256 bytes: the kernel stages R into shared memory in 16-byte pieces
+    if (cudaMalloc(&ctx->d_rcanon, align_up(nent, 256)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_rpacked_buf, align_up(nent / 2, 256) + 256) != cudaSuccess) {
+        cudaGetLastError();
+        fold_destroy(ctx);
+        return FOLD_ENOMEM;
+    }
+    ctx->d_rpacked = q >= 10 ? ctx->d_rpacked_buf : ctx->d_rcanon;
+    cudaError_t e = launch_rtable(q, ctx->d_rcanon, ctx->d_rpacked_buf, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        fold_destroy(ctx);
+        return FOLD_ECUDA;
+    }
+    ctx->launches = 1;
+    *out = ctx;
+    return FOLD_OK;
+}
+
+void fold_destroy(fold_ctx *ctx) {
+    if (!ctx) return;
+    fold_serve_stop(ctx);
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto &kv : ctx->sched_cache) cudaFree(kv.second.dev);
+    if (ctx->d_rcanon) cudaFree(ctx->d_rcanon);
+    if (ctx->d_rpacked_buf) cudaFree(ctx->d_rpacked_buf);
+    if (ctx->ws.ptr) cudaFree(ctx->ws.ptr);
+    if (ctx->aux.ptr) cudaFree(ctx->aux.ptr);
+    if (ctx->dout.ptr) cudaFree(ctx->dout.ptr);
+    if (ctx->hstage.ptr) cudaFreeHost(ctx->hstage.ptr);
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+int fold_set_option(fold_ctx *ctx, int option, int64_t value) {
+    if (!ctx) return FOLD_EINVAL;
+    switch (option) {
+        case FOLD_OPT_METHOD:
+            if (value != FOLD_METHOD_TWO_VECTOR && value != FOLD_METHOD_PLAIN) return FOLD_EINVAL;
+            ctx->method = (int)value;
+            return FOLD_OK;
+        case FOLD_OPT_GRID:
+            if (value < 0 || value > 1 << 20) return FOLD_EINVAL;
+            ctx->grid_override = (int)value;
+            return FOLD_OK;
+        case FOLD_OPT_TIMEOUT_MS:
+            if (value < 1 || value > 600000) return FOLD_EINVAL;
+            ctx->timeout_ms = value;
+            return FOLD_OK;
+        case FOLD_OPT_KCHUNK:
+            if (value < 0 || value > 4096) return FOLD_EINVAL;
+            ctx->kc_override = (int)value;
+            return FOLD_OK;
+        case FOLD_OPT_TEST_DROP_TASK:
+            if (value < 0 || value > 1) return FOLD_EINVAL;
+            ctx->test_drop_task = (int)value;
+            return FOLD_OK;
+    }
+    return FOLD_EINVAL;
+}
+
+int fold_get_option(fold_ctx *ctx, int option, int64_t *value) {
+    if (!ctx || !value) return FOLD_EINVAL;
+    switch (option) {
+        case FOLD_OPT_METHOD: *value = ctx->method; return FOLD_OK;
+        case FOLD_OPT_GRID: *value = grid_for(ctx); return FOLD_OK;
+        case FOLD_OPT_TIMEOUT_MS: *value = ctx->timeout_ms; return FOLD_OK;
+        case FOLD_OPT_KCHUNK: *value = ctx->kc_override; return FOLD_OK;
+        case FOLD_OPT_Q: *value = ctx->q; return FOLD_OK;
+        case FOLD_OPT_TILE: *value = tile_of(ctx->q, ctx->method); return FOLD_OK;
+        case FOLD_OPT_LAUNCHES: *value = (int64_t)ctx->launches; return FOLD_OK;
+        case FOLD_OPT_TEST_DROP_TASK: *value = ctx->test_drop_task; return FOLD_OK;
+    }
+    return FOLD_EINVAL;
+}
+
+int fold_rtable(fold_ctx *ctx, uint8_t *out, int64_t cap) {
+    if (!ctx || !out) return FOLD_EINVAL;
+    int64_t nent = (int64_t)1 << (2 * (ctx->q - 1));
+    if (cap < nent) return FOLD_EINVAL;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaMemcpy(out, ctx->d_rcanon, (size_t)nent, cudaMemcpyDeviceToHost);
+    return status_from_cuda(e);
+}
+
+int64_t fold_workspace_bytes(fold_ctx *ctx, int32_t n) {
+    if (!ctx || n < 0 || n > FOLD_MAX_N) return -FOLD_EINVAL;
+    Plan pl = make_plan(&n, 1, ctx->q, ctx->method);
+    return (int64_t)pl.bytes;
+}
+
+int fold_score_dev(fold_ctx *ctx, const uint8_t *d_codes, int32_t n, void *d_ws, int64_t ws_bytes,
+                   int32_t *d_max_pairs, int16_t *d_D_out, void *stream) {
+    if (!ctx || !d_ws || !d_max_pairs || n < 0 || n > FOLD_MAX_N || (n > 0 && !d_codes)) return FOLD_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_ws) & 255) != 0) return FOLD_EINVAL;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    return enqueue_single(ctx, d_codes, n, reinterpret_cast<uint8_t *>(d_ws), (size_t)ws_bytes, d_max_pairs,
+                          d_D_out, st);
+}
+
+int fold_score(fold_ctx *ctx, const char *seq, int32_t n, int32_t *max_pairs, int16_t *D_out) {
+    if (!ctx || !max_pairs || n < 0 || n > FOLD_MAX_N || (n > 0 && !seq)) return FOLD_EINVAL;
+    cudaSetDevice(ctx->device);
+    size_t hbytes = (size_t)std::max(n, 1) + 256;
+    if (ensure_host(ctx->hstage, hbytes)) return FOLD_ENOMEM;
+    uint8_t *hcodes = reinterpret_cast<uint8_t *>(ctx->hstage.ptr);
+    int32_t *hres = reinterpret_cast<int32_t *>(hcodes + align_up((size_t)std::max(n, 1), 64));
+    if (!encode_seq(seq, n, hcodes)) return FOLD_EINVAL;
+    Plan pl = make_plan(&n, 1, ctx->q, ctx->method);
+    size_t aux_bytes = align_up((size_t)std::max(n, 1), 256) + 256;
+    if (ensure_buf(ctx->ws, pl.bytes) || ensure_buf(ctx->aux, aux_bytes)) return FOLD_ENOMEM;
+    if (D_out && n > 0 && ensure_buf(ctx->dout, (size_t)n * n * 2)) return FOLD_ENOMEM;
+    uint8_t *dcodes = reinterpret_cast<uint8_t *>(ctx->aux.ptr);
+    int32_t *dres = reinterpret_cast<int32_t *>(dcodes + align_up((size_t)std::max(n, 1), 256));
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaSuccess;
+    if (n > 0) e = cudaMemcpyAsync(dcodes, hcodes, (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    int rc = enqueue_single(ctx, dcodes, n, reinterpret_cast<uint8_t *>(ctx->ws.ptr), ctx->ws.bytes, dres,
+                            (D_out && n > 0) ? reinterpret_cast<int16_t *>(ctx->dout.ptr) : nullptr, st);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(hres, dres, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && D_out && n > 0)
+        e = cudaMemcpyAsync(D_out, ctx->dout.ptr, (size_t)n * n * 2, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    if (*hres < 0) return -*hres == FOLD_ETIMEOUT ? FOLD_ETIMEOUT : FOLD_ECUDA;
+    *max_pairs = *hres;
+    return FOLD_OK;
+}
+
+int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int32_t *lens, int32_t *max_pairs_out,
+               int16_t *const *D_out) {
+    if (!ctx || count < 0 || (count > 0 && (!seqs || !lens || !max_pairs_out))) return FOLD_EINVAL;
+    if (count == 0) return FOLD_OK;
+    for (int k = 0; k < count; ++k)
+        if (lens[k] < 0 || lens[k] > FOLD_MAX_N || (lens[k] > 0 && !seqs[k])) return FOLD_EINVAL;
+    cudaSetDevice(ctx->device);
+    Plan pl = make_plan(lens, count, ctx->q, ctx->method);
+    int maxNT = 0;
+    for (int v : pl.NTs) maxNT = std::max(maxNT, v);
+    int kc = ctx->kc_override > 0 ? ctx->kc_override : kc_auto(maxNT);
+    std::vector<int4> tv;
+    build_schedule(pl.NTs, kc, tv);
+    // host staging: codes (padded) | SeqDesc | tasks | results
+    size_t codes_bytes = pl.off_drow - pl.off_codes;
+    size_t sd_bytes = align_up(sizeof(SeqDesc) * count, 256);
+    size_t task_bytes = align_up(tv.size() * sizeof(int4), 256);
+    size_t res_bytes = align_up(4 * (size_t)count, 256);
+    if (ensure_host(ctx->hstage, codes_bytes + sd_bytes + task_bytes + res_bytes)) return FOLD_ENOMEM;
+    uint8_t *h = reinterpret_cast<uint8_t *>(ctx->hstage.ptr);
+    uint8_t *hcodes = h;
+    memset(hcodes, kPadCode, codes_bytes);
+    for (int k = 0; k < count; ++k)
+        if (!encode_seq(seqs[k], lens[k], hcodes + pl.sd[k].code_off)) return FOLD_EINVAL;
+    memcpy(h + codes_bytes, pl.sd.data(), sizeof(SeqDesc) * count);
+    if (!tv.empty()) memcpy(h + codes_bytes + sd_bytes, tv.data(), tv.size() * sizeof(int4));
+    int32_t *hres = reinterpret_cast<int32_t *>(h + codes_bytes + sd_bytes + task_bytes);
+    if (ensure_buf(ctx->ws, pl.bytes) || ensure_buf(ctx->aux, sd_bytes + task_bytes + res_bytes)) return FOLD_ENOMEM;
+    uint8_t *ws = reinterpret_cast<uint8_t *>(ctx->ws.ptr);
+    uint8_t *aux = reinterpret_cast<uint8_t *>(ctx->aux.ptr);
+    SeqDesc *d_sd = reinterpret_cast<SeqDesc *>(aux);
+    int4 *d_tasks = reinterpret_cast<int4 *>(aux + sd_bytes);
+    int32_t *d_res = reinterpret_cast<int32_t *>(aux + sd_bytes + task_bytes);
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaMemsetAsync(ws, 0, pl.zero_bytes, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ws + pl.off_codes, hcodes, codes_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(aux, h + codes_bytes, sd_bytes + task_bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    FoldParams p = make_params(ctx, pl, ws, d_tasks, (int)tv.size(), d_sd);
+    if (!tv.empty()) {
+        e = launch_fold(p, ctx->q, ctx->method, grid_for(ctx), st);
+        if (e != cudaSuccess) return status_from_cuda(e);
+        ctx->launches += 1;
+    }
+    e = launch_finalize(p.error, p.results, count, d_res, st);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    ctx->launches += 1;
+    e = cudaMemcpyAsync(hres, d_res, 4 * (size_t)count, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    int status = FOLD_OK;
+    for (int k = 0; k < count; ++k) {
+        if (hres[k] < 0) status = -hres[k] == FOLD_ETIMEOUT ? FOLD_ETIMEOUT : FOLD_ECUDA;
+        max_pairs_out[k] = lens[k] >= 2 ? hres[k] : 0;
+    }
+    if (status) return status;
+    if (D_out) {
+        for (int k = 0; k < count; ++k) {
+            int n = lens[k];
+            if (!D_out[k] || n == 0) continue;
+            if (ensure_buf(ctx->dout, (size_t)n * n * 2)) return FOLD_ENOMEM;
+            e = launch_extract(p.drow + pl.sd[k].drow_off, pl.sd[k].Np, n, reinterpret_cast<int16_t *>(ctx->dout.ptr), st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(D_out[k], ctx->dout.ptr, (size_t)n * n * 2, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return status_from_cuda(e);
+            ctx->launches += 1;
+        }
+    }
+    return FOLD_OK;
+}
+
+}  // extern "C"

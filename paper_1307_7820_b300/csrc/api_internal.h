@@ -1,0 +1,68 @@
+// api_internal.h -- context and planning structures shared by api.cu and
+// serve.cu (internal to libfold_b300).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <vector>
+
+#include "fold_common.h"
+
+namespace fold {
+
+struct DevBuf { void *ptr = nullptr; size_t bytes = 0; };
+struct HostBuf { void *ptr = nullptr; size_t bytes = 0; };
+
+struct CachedSched {
+    void *dev = nullptr;
+    SeqDesc *d_sd = nullptr;
+    int4 *d_tasks = nullptr;
+    int ntasks = 0;
+};
+
+// Workspace layout of a set of sequences (byte offsets into one buffer).
+struct Plan {
+    int q = 8, method = 0, T = 32, count = 0;
+    std::vector<SeqDesc> sd;
+    std::vector<int> NTs;
+    size_t off_control = 0, off_results = 0, off_flags = 0, off_cnt = 0, off_pring = 0;
+    size_t off_codes = 0, off_drow = 0, off_dcol = 0, off_rf = 0, off_cf = 0;
+    size_t zero_bytes = 0, bytes = 0;
+};
+
+struct ServeState;  // serve.cu
+
+}  // namespace fold
+
+struct fold_ctx {
+    int device = 0;
+    int q = 8;
+    int method = 0;
+    uint16_t pair_mask = 0;
+    unsigned long long pair64 = 0;
+    int sm_count = 1;
+    int grid_override = 0;
+    int kc_override = 0;
+    long long timeout_ms = 5000;
+    int test_drop_task = 0;
+    cudaStream_t stream = nullptr;
+    uint8_t *d_rcanon = nullptr;
+    uint8_t *d_rpacked_buf = nullptr;
+    const uint8_t *d_rpacked = nullptr;
+    std::map<long long, fold::CachedSched> sched_cache;
+    fold::DevBuf ws, aux, dout;
+    fold::HostBuf hstage;
+    unsigned long long launches = 0;
+    fold::ServeState *serve = nullptr;
+};
+
+namespace fold {
+Plan make_plan(const int32_t *lens, int count, int q, int method);
+FoldParams make_params(const fold_ctx *ctx, const Plan &pl, uint8_t *ws, const int4 *tasks, int ntasks,
+                       const SeqDesc *d_sd);
+int grid_for(fold_ctx *ctx);
+int kc_auto(int NT);
+int status_from_cuda(cudaError_t e);
+bool encode_seq(const char *seq, int n, uint8_t *out);
+}  // namespace fold

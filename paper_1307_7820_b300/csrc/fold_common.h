@@ -1,0 +1,79 @@
+// fold_common.h -- internal layout and task definitions shared by the host
+// scheduler and the CUDA kernels of libfold_b300 (not part of the public ABI).
+//
+// The DP table of one sequence (Section 2, Eq. 1) is padded to Np = NT*T
+// positions (padding bases never pair) and cut into T x T tiles; tile (I,J)
+// holds rows I*T.. and columns J*T.. .  T is a multiple of q, so tile borders
+// are group borders: column group g covers columns g*q..g*q+q-1 and its row
+// group covers rows g*q+1..g*q+q (Section 3.1).
+#pragma once
+#include <stdint.h>
+
+namespace fold {
+
+constexpr int kWarpsPerCta = 8;                 // warp-level workers per CTA
+constexpr int kThreads = 32 * kWarpsPerCta;
+constexpr int kColOff = 7;                      // Dcol offset: D(i,j) at Dcol[j*PC + i + 7]
+constexpr int kRing = 8;                        // P (far partial max) ring depth in tile diagonals
+constexpr int kNeg16 = -32768;                  // int16 "minus infinity" for the row closure
+constexpr int kPadCode = 4;                     // padding base: pairs with nothing
+
+enum Method : int { kTwoVector = 0, kPlain = 1 };
+enum TaskType : int { kTaskNear = 0, kTaskFar = 1 };
+
+// tile edge for a given q (two-vector) or the plain kernel
+__host__ __device__ constexpr int tile_of(int q, int method) {
+    return method == kPlain ? 32 : q * (32 / q);
+}
+__host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Task word layout (int4): x = sequence index; y = type<<28 | I<<14 | J;
+// NEAR: z = number of FAR chunks that feed the tile; FAR: z = Ka, w = Kb
+// (inclusive tile-column range of the middle blocks).
+__host__ __device__ inline int task_type(int y) { return (y >> 28) & 3; }
+__host__ __device__ inline int task_I(int y) { return (y >> 14) & 0x3fff; }
+__host__ __device__ inline int task_J(int y) { return y & 0x3fff; }
+__host__ __device__ inline int task_pack(int type, int I, int J) { return (type << 28) | (I << 14) | J; }
+
+// Per-sequence descriptor (device).  Offsets are in elements of the pools.
+struct SeqDesc {
+    int n;          // true length
+    int NT;         // tiles per side
+    int Np;         // NT*T
+    int PC;         // column pitch of the column-major copy
+    long long code_off;   // uint8 codes (Np entries, padding = kPadCode)
+    long long drow_off;   // int16 row-major copy, Np*Np
+    long long dcol_off;   // int16 column-major copy, Np*PC
+    long long rf_off;     // uint32 row features, Np rows * (Np/q) groups
+    long long cf_off;     // uint32 column features, (Np/q) groups * Np columns
+    long long flag_off;   // int tile-done flags, NT*NT
+    long long cnt_off;    // int far-chunk counters, NT*NT
+    long long p_off;      // int P ring, kRing*NT*T*T
+    int result_index;     // results[result_index] = D(0, n-1)
+    int pad_;
+};
+
+struct FoldParams {
+    const int4 *tasks;
+    int ntasks;
+    int *queue_head;          // next task index
+    int *error;               // first error code (0 = none) and where
+    const SeqDesc *seqs;
+    const uint8_t *codes;
+    int16_t *drow;
+    int16_t *dcol;
+    uint32_t *rf;
+    uint32_t *cf;
+    int *flags;
+    int *cnt;
+    int *pring;
+    int *results;
+    const uint8_t *rtab;      // R table in the kernel's smem layout
+    unsigned long long pair64;  // bit (8x+y) = b(x,y)
+    long long timeout_ns;     // bound on every device-side wait
+};
+
+// error word values written by the kernel
+enum KernelError : int { kErrNone = 0, kErrTimeout = 1, kErrBadTask = 2 };
+
+}  // namespace fold

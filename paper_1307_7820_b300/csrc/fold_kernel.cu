@@ -1,0 +1,172 @@
+// fold_kernel.cu -- small kernels of libfold_b300 and the dispatch to the
+// per-instantiation launchers (fold_inst_*.cu).
+//
+//   rtable_build_kernel   Section 3.1 preprocessing: one thread per pair of
+//                         (q-1)-bit difference vectors.
+//   extract / pad / finalize   data movement around the persistent kernel.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fold_common.h"
+#include "kernels.h"
+
+namespace fold {
+
+#define FOLD_INST_DECL(NAME) \
+    cudaError_t launch_##NAME(const FoldParams &p, int grid, cudaStream_t st); \
+    int bps_##NAME(); \
+    size_t smem_##NAME();
+FOLD_INST_DECL(tv2)
+FOLD_INST_DECL(tv3)
+FOLD_INST_DECL(tv4)
+FOLD_INST_DECL(tv5)
+FOLD_INST_DECL(tv6)
+FOLD_INST_DECL(tv7)
+FOLD_INST_DECL(tv8)
+FOLD_INST_DECL(tv9)
+FOLD_INST_DECL(tv10)
+FOLD_INST_DECL(plain)
+
+// ------------------------------------------------------------------ R table
+// R[(h << (q-1)) | c] = max over k in [0,q-1] of sum_{p<=k} (h_p - c_p), with
+// h_0 = c_0 = 0 (the scan of the preprocessing routine, strict '>' from 0).
+__global__ void rtable_build_kernel(int q, uint8_t *canon, uint8_t *packed) {
+    int nb = q - 1;
+    long long nent = 1LL << (2 * nb);
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nent;
+         idx += (long long)gridDim.x * blockDim.x) {
+        unsigned h = (unsigned)(idx >> nb), c = (unsigned)(idx & ((1u << nb) - 1));
+        int best = 0, sum = 0;
+        for (int p = 1; p <= nb; ++p) {
+            sum += (int)((h >> (p - 1)) & 1u) - (int)((c >> (p - 1)) & 1u);
+            if (sum > best) best = sum;
+        }
+        canon[idx] = (uint8_t)best;
+    }
+    // packed form used by the kernel: bytes for q <= 9, nibbles for q = 10
+    if (q >= 10) {
+        for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nent / 2;
+             b += (long long)gridDim.x * blockDim.x) {
+            unsigned h = (unsigned)((2 * b) >> nb), c0 = (unsigned)((2 * b) & ((1u << nb) - 1));
+            int v[2];
+            for (int e = 0; e < 2; ++e) {
+                unsigned c = c0 + e;
+                int best = 0, sum = 0;
+                for (int p = 1; p <= nb; ++p) {
+                    sum += (int)((h >> (p - 1)) & 1u) - (int)((c >> (p - 1)) & 1u);
+                    if (sum > best) best = sum;
+                }
+                v[e] = best;
+            }
+            packed[b] = (uint8_t)(v[0] | (v[1] << 4));
+        }
+    }
+}
+
+// ---------------------------------------------------------------- extract
+// Dense n*n row-major copy of the upper triangle (0 below the diagonal).
+__global__ void extract_kernel(const int16_t *drow, int Np, int n, int16_t *out) {
+    long long total = (long long)n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(e / n), jj = (int)(e % n);
+        out[e] = (i <= jj) ? drow[(size_t)i * Np + jj] : (int16_t)0;
+    }
+}
+
+// Pads 2-bit codes to Np with the padding code.
+__global__ void pad_codes_kernel(const uint8_t *in, int n, int Np, uint8_t *out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Np; e += gridDim.x * blockDim.x)
+        out[e] = (e < n) ? in[e] : (uint8_t)kPadCode;
+}
+
+// ---------------------------------------------------------------- host side
+size_t fold_smem_bytes(int q, int method) {
+    if (method == kPlain) return smem_plain();
+    switch (q) {
+        case 2: return smem_tv2();
+        case 3: return smem_tv3();
+        case 4: return smem_tv4();
+        case 5: return smem_tv5();
+        case 6: return smem_tv6();
+        case 7: return smem_tv7();
+        case 8: return smem_tv8();
+        case 9: return smem_tv9();
+        case 10: return smem_tv10();
+    }
+    return 0;
+}
+
+int fold_blocks_per_sm(int q, int method) {
+    if (method == kPlain) return bps_plain();
+    switch (q) {
+        case 2: return bps_tv2();
+        case 3: return bps_tv3();
+        case 4: return bps_tv4();
+        case 5: return bps_tv5();
+        case 6: return bps_tv6();
+        case 7: return bps_tv7();
+        case 8: return bps_tv8();
+        case 9: return bps_tv9();
+        case 10: return bps_tv10();
+    }
+    return 0;
+}
+
+// Writes the answers (or -status if any device-side wait failed).
+__global__ void finalize_kernel(const int *error, const int *results, int count, int32_t *out) {
+    int e = *(volatile const int *)error;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x)
+        out[k] = e == kErrNone ? results[k] : (e == kErrTimeout ? -4 : -1);
+}
+
+cudaError_t launch_finalize(const int *error, const int *results, int count, int32_t *out, cudaStream_t st) {
+    int blocks = (count + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 1024) blocks = 1024;
+    finalize_kernel<<<blocks, 256, 0, st>>>(error, results, count, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold(const FoldParams &p, int q, int method, int grid, cudaStream_t st) {
+    if (method == kPlain) return launch_plain(p, grid, st);
+    switch (q) {
+        case 2: return launch_tv2(p, grid, st);
+        case 3: return launch_tv3(p, grid, st);
+        case 4: return launch_tv4(p, grid, st);
+        case 5: return launch_tv5(p, grid, st);
+        case 6: return launch_tv6(p, grid, st);
+        case 7: return launch_tv7(p, grid, st);
+        case 8: return launch_tv8(p, grid, st);
+        case 9: return launch_tv9(p, grid, st);
+        case 10: return launch_tv10(p, grid, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rtable(int q, uint8_t *canon, uint8_t *packed, cudaStream_t st) {
+    long long nent = 1LL << (2 * (q - 1));
+    int blocks = (int)((nent + 255) / 256);
+    if (blocks > 1024) blocks = 1024;
+    rtable_build_kernel<<<blocks, 256, 0, st>>>(q, canon, packed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extract(const int16_t *drow, int Np, int n, int16_t *out, cudaStream_t st) {
+    long long total = (long long)n * n;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    extract_kernel<<<blocks, 256, 0, st>>>(drow, Np, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad_codes(const uint8_t *in, int n, int Np, uint8_t *out, cudaStream_t st) {
+    int blocks = (Np + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    if (blocks < 1) blocks = 1;
+    pad_codes_kernel<<<blocks, 256, 0, st>>>(in, n, Np, out);
+    return cudaGetLastError();
+}
+
+}  // namespace fold

@@ -1,0 +1,18 @@
+// kernels.h -- host launchers for the kernels in fold_kernel.cu (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fold_common.h"
+
+namespace fold {
+
+size_t fold_smem_bytes(int q, int method);
+int fold_blocks_per_sm(int q, int method);
+cudaError_t launch_finalize(const int *error, const int *results, int count, int32_t *out, cudaStream_t st);
+cudaError_t launch_fold(const FoldParams &p, int q, int method, int grid, cudaStream_t st);
+cudaError_t launch_rtable(int q, uint8_t *canon, uint8_t *packed, cudaStream_t st);
+cudaError_t launch_extract(const int16_t *drow, int Np, int n, int16_t *out, cudaStream_t st);
+cudaError_t launch_pad_codes(const uint8_t *in, int n, int Np, uint8_t *out, cudaStream_t st);
+
+}  // namespace fold

@@ -1,0 +1,256 @@
+"""Thin ctypes binding of libfold_b300 (C-ABI in include/fold.h).
+
+Every function here only marshals arguments: each step of the fold runs in
+the CUDA library.  The functions keep the C names (``fold_init``,
+``fold_score``, ...); :class:`Folder` wraps a context for convenience.  The
+library is loaded from this directory; if it is missing, :func:`lib` raises
+instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfold_b300.so")
+
+FOLD_OK, FOLD_EINVAL, FOLD_ENOMEM, FOLD_EAGAIN, FOLD_ETIMEOUT, FOLD_ECUDA, FOLD_ENOTREADY = range(7)
+FOLD_METHOD_TWO_VECTOR, FOLD_METHOD_PLAIN = 0, 1
+FOLD_OPT_METHOD, FOLD_OPT_GRID, FOLD_OPT_TIMEOUT_MS, FOLD_OPT_KCHUNK = 1, 2, 3, 4
+FOLD_OPT_Q, FOLD_OPT_TILE, FOLD_OPT_LAUNCHES, FOLD_OPT_TEST_DROP_TASK = 5, 6, 7, 8
+FOLD_PAIRS_DEFAULT = 0x5A48   # AU UA CG GC GU UG
+FOLD_PAIRS_PAPER = 0x1248     # AU UA CG GC
+FOLD_MAX_N = 65535
+
+#: every symbol include/fold.h declares
+ABI_SYMBOLS = (
+    "fold_init", "fold_destroy", "fold_strerror", "fold_set_option", "fold_get_option", "fold_rtable",
+    "fold_score", "fold_workspace_bytes", "fold_score_dev", "fold_batch",
+    "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop",
+)
+
+_lib = None
+
+
+class FoldError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = fold_strerror(code) if _lib is not None else f"status {code}"
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+
+
+def lib():
+    """Load libfold_b300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1307_7820_b300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u16 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint16
+    P = ctypes.POINTER
+    L.fold_init.argtypes = [ctypes.c_int, u16, ctypes.c_int, P(vp)]
+    L.fold_init.restype = ctypes.c_int
+    L.fold_destroy.argtypes = [vp]
+    L.fold_destroy.restype = None
+    L.fold_strerror.argtypes = [ctypes.c_int]
+    L.fold_strerror.restype = ctypes.c_char_p
+    L.fold_set_option.argtypes = [vp, ctypes.c_int, i64]
+    L.fold_get_option.argtypes = [vp, ctypes.c_int, P(i64)]
+    L.fold_rtable.argtypes = [vp, vp, i64]
+    L.fold_score.argtypes = [vp, ctypes.c_char_p, i32, P(i32), vp]
+    L.fold_workspace_bytes.argtypes = [vp, i32]
+    L.fold_workspace_bytes.restype = i64
+    L.fold_score_dev.argtypes = [vp, vp, i32, vp, i64, vp, vp, vp]
+    L.fold_batch.argtypes = [vp, i32, P(ctypes.c_char_p), P(i32), P(i32), P(vp)]
+    L.fold_serve_start.argtypes = [vp, i64, i32]
+    L.fold_serve_submit.argtypes = [vp, ctypes.c_char_p, i32, P(ctypes.c_uint64)]
+    L.fold_serve_poll.argtypes = [vp, ctypes.c_uint64, P(i32), vp]
+    L.fold_serve_stop.argtypes = [vp]
+    for name in ("fold_set_option", "fold_get_option", "fold_rtable", "fold_score", "fold_score_dev", "fold_batch",
+                 "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != FOLD_OK:
+        raise FoldError(rc, what)
+
+
+# ---------------------------------------------------------------- C names
+def fold_strerror(code: int) -> str:
+    return lib().fold_strerror(code).decode()
+
+
+def fold_init(q: int = 8, pair_mask: int = FOLD_PAIRS_DEFAULT, device: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().fold_init(q, pair_mask, device, ctypes.byref(h)), "fold_init")
+    return h.value
+
+
+def fold_destroy(ctx: int) -> None:
+    lib().fold_destroy(ctx)
+
+
+def fold_set_option(ctx: int, option: int, value: int) -> None:
+    _check(lib().fold_set_option(ctx, option, value), "fold_set_option")
+
+
+def fold_get_option(ctx: int, option: int) -> int:
+    v = ctypes.c_int64()
+    _check(lib().fold_get_option(ctx, option, ctypes.byref(v)), "fold_get_option")
+    return v.value
+
+
+def fold_rtable(ctx: int) -> np.ndarray:
+    q = fold_get_option(ctx, FOLD_OPT_Q)
+    out = np.zeros(1 << (2 * (q - 1)), dtype=np.uint8)
+    _check(lib().fold_rtable(ctx, out.ctypes.data, out.size), "fold_rtable")
+    return out
+
+
+def fold_score(ctx: int, seq: str, want_D: bool = False):
+    """D(0,n-1) (and the n*n int16 table if want_D) for a host string."""
+    b = seq.encode("ascii")
+    n = len(b)
+    mp = ctypes.c_int32()
+    D = np.zeros((n, n), dtype=np.int16) if want_D else None
+    _check(lib().fold_score(ctx, b, n, ctypes.byref(mp), D.ctypes.data if want_D and n else None), "fold_score")
+    return (mp.value, D) if want_D else mp.value
+
+
+def fold_workspace_bytes(ctx: int, n: int) -> int:
+    v = lib().fold_workspace_bytes(ctx, n)
+    if v < 0:
+        raise FoldError(-v, "fold_workspace_bytes")
+    return v
+
+
+def fold_score_dev(ctx: int, d_codes: int, n: int, d_ws: int, ws_bytes: int, d_max_pairs: int,
+                   d_D_out: int | None = None, stream: int | None = None) -> None:
+    """Enqueue a fold on device pointers (ints, e.g. torch ``data_ptr()``)."""
+    _check(lib().fold_score_dev(ctx, d_codes, n, d_ws, ws_bytes, d_max_pairs, d_D_out, stream), "fold_score_dev")
+
+
+def fold_batch(ctx: int, seqs, want_D: bool = False):
+    bs = [s.encode("ascii") for s in seqs]
+    k = len(bs)
+    arr = (ctypes.c_char_p * k)(*bs)
+    lens = (ctypes.c_int32 * k)(*[len(x) for x in bs])
+    out = (ctypes.c_int32 * k)()
+    Ds = None
+    dptr = None
+    if want_D:
+        Ds = [np.zeros((len(x), len(x)), dtype=np.int16) for x in bs]
+        dptr = (ctypes.c_void_p * k)(*[D.ctypes.data if D.size else None for D in Ds])
+    _check(lib().fold_batch(ctx, k, arr, lens, out, dptr), "fold_batch")
+    res = np.array(list(out), dtype=np.int32)
+    return (res, Ds) if want_D else res
+
+
+def fold_serve_start(ctx: int, budget_bytes: int, max_inflight: int = 4096) -> None:
+    _check(lib().fold_serve_start(ctx, budget_bytes, max_inflight), "fold_serve_start")
+
+
+def fold_serve_submit(ctx: int, seq: str) -> int:
+    """Ticket, or raises FoldError(FOLD_EAGAIN) when the request must wait."""
+    b = seq.encode("ascii")
+    t = ctypes.c_uint64()
+    _check(lib().fold_serve_submit(ctx, b, len(b), ctypes.byref(t)), "fold_serve_submit")
+    return t.value
+
+
+def fold_serve_poll(ctx: int, ticket: int, D_out: np.ndarray | None = None):
+    """max pairs once done, None while the request is in flight."""
+    mp = ctypes.c_int32()
+    rc = lib().fold_serve_poll(ctx, ticket, ctypes.byref(mp), D_out.ctypes.data if D_out is not None else None)
+    if rc == FOLD_ENOTREADY:
+        return None
+    _check(rc, "fold_serve_poll")
+    return mp.value
+
+
+def fold_serve_stop(ctx: int) -> None:
+    _check(lib().fold_serve_stop(ctx), "fold_serve_stop")
+
+
+# ---------------------------------------------------------------- convenience
+class Folder:
+    """A context: ``Folder(q=8).score("GGGAAAUCC")``."""
+
+    def __init__(self, q: int = 8, pair_mask: int = FOLD_PAIRS_DEFAULT, device: int = 0, method: str = "two_vector"):
+        self.ctx = fold_init(q, pair_mask, device)
+        self.set_method(method)
+
+    def set_method(self, method: str) -> None:
+        fold_set_option(self.ctx, FOLD_OPT_METHOD,
+                        {"two_vector": FOLD_METHOD_TWO_VECTOR, "plain": FOLD_METHOD_PLAIN}[method])
+
+    @property
+    def q(self) -> int:
+        return fold_get_option(self.ctx, FOLD_OPT_Q)
+
+    @property
+    def tile(self) -> int:
+        return fold_get_option(self.ctx, FOLD_OPT_TILE)
+
+    @property
+    def launches(self) -> int:
+        return fold_get_option(self.ctx, FOLD_OPT_LAUNCHES)
+
+    def option(self, opt: int, value: int | None = None):
+        if value is None:
+            return fold_get_option(self.ctx, opt)
+        fold_set_option(self.ctx, opt, value)
+
+    def rtable(self) -> np.ndarray:
+        return fold_rtable(self.ctx)
+
+    def score(self, seq: str, want_D: bool = False):
+        return fold_score(self.ctx, seq, want_D)
+
+    def batch(self, seqs, want_D: bool = False):
+        return fold_batch(self.ctx, seqs, want_D)
+
+    def workspace_bytes(self, n: int) -> int:
+        return fold_workspace_bytes(self.ctx, n)
+
+    def score_dev(self, codes, ws, out, D_out=None, stream=None) -> None:
+        """codes: uint8 CUDA tensor of codes 0..3; ws: uint8 CUDA tensor of
+        workspace_bytes(n); out: int32 CUDA tensor (1 element)."""
+        n = int(codes.numel())
+        fold_score_dev(self.ctx, codes.data_ptr() if n else None, n, ws.data_ptr(), ws.numel(), out.data_ptr(),
+                       D_out.data_ptr() if D_out is not None else None, stream)
+
+    def close(self) -> None:
+        if self.ctx:
+            fold_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def encode_codes(seq: str) -> np.ndarray:
+    """Base letters to codes 0..3 (for the device path); raises on other letters."""
+    b = np.frombuffer(seq.encode("ascii"), dtype=np.uint8)
+    lut = np.full(256, 255, dtype=np.uint8)
+    for ch, v in zip(b"ACGUacgu", (0, 1, 2, 3, 0, 1, 2, 3)):
+        lut[ch] = v
+    c = lut[b]
+    if c.size and c.max() == 255:
+        raise ValueError("invalid base letter")
+    return c

@@ -1,0 +1,59 @@
+"""C-ABI checks that need no GPU: the library loads and exports every symbol
+include/fold.h declares; status strings; argument validation paths that
+return before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1307_7820_b300 import build as fbuild
+from paper_1307_7820_b300 import fold
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fold.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fold_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    fbuild.build()
+    return fold.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(L, name), name
+    assert sorted(fold.ABI_SYMBOLS) == names
+
+
+def test_strerror_all_codes(L):
+    for code in range(7):
+        s = fold.fold_strerror(code)
+        assert s and s != "unknown status"
+    assert fold.fold_strerror(99) == "unknown status"
+
+
+def test_null_and_range_arguments(L):
+    # all of these are rejected on the host before any device work
+    assert L.fold_init(3, 0x5A48, 0, None) == fold.FOLD_EINVAL
+    h = ctypes.c_void_p()
+    assert L.fold_init(11, 0x5A48, 0, ctypes.byref(h)) == fold.FOLD_EINVAL
+    assert L.fold_init(1, 0x5A48, 0, ctypes.byref(h)) == fold.FOLD_EINVAL
+    assert L.fold_init(8, 0x5A48, -1, ctypes.byref(h)) == fold.FOLD_EINVAL
+    assert L.fold_score(None, b"AU", 2, None, None) == fold.FOLD_EINVAL
+    assert L.fold_set_option(None, fold.FOLD_OPT_METHOD, 0) == fold.FOLD_EINVAL
+    assert L.fold_workspace_bytes(None, 10) == -fold.FOLD_EINVAL
+    assert L.fold_batch(None, 1, None, None, None, None) == fold.FOLD_EINVAL
+
+
+def test_pair_mask_constants():
+    import oracle
+    assert fold.FOLD_PAIRS_DEFAULT == oracle.MASK6
+    assert fold.FOLD_PAIRS_PAPER == oracle.MASK4
