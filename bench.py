@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Benchmark: two-vector Four-Russians Nussinov folding on one B300 per rank.
+
+Prints ONE JSON line (rank 0).  The headline is DP cells/s of one fold of a
+single n = 6000 uniform-ACGU sequence (q = 8, pair set AU UA CG GC GU UG),
+device-resident inputs, L2 flushed between steps; beside it the plain
+Nussinov kernel on the same input, the end-to-end host-buffer call, batched
+and served throughput, the lookup roofline of the persistent kernel, SM
+clocks sampled during the timed region, and the CPU oracle baseline.
+
+A step is one complete fold (every cell of the table).  With --gpus N > 1
+(torchrun, one rank per GPU) every rank folds its own replica of the
+workload (a single fold does not shard); value = all ranks' cells / max time.
+
+--impl reference times the CPU oracle (the plain cubic recurrence) on the
+host cores instead, on a bounded prefix of the same input per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DP cells/s at n=6000 vs plain GPU Nussinov; batched seq/s; serve p50/p99 ms"
+UNIT = "cells/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=6000)
+    ap.add_argument("--q", type=int, default=8)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--trace", default="", help="write a per-task trace of one fold to this .npy file")
+    return ap.parse_args()
+
+
+def workload_config(a):
+    return {
+        "workload": f"single RNA sequence n={a.n}, i.i.d. uniform ACGU (seed 1308), pair set AU,UA,CG,GC,GU,UG, "
+                    f"no minimum hairpin, two-vector q={a.q}, int16 D stored row- and column-major",
+        "n": a.n,
+        "q": a.q,
+        "pair_mask": "0x5A48",
+        "seed": 1308,
+        "l2": "flushed between timed steps by a 256 MiB device write outside the timed events",
+        "replicas": "each rank folds its own copy (a single fold does not shard)",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+                power.append(float(p[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "power_w_max": max(power),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU side
+def cpu_oracle_sample(seq: str, prefix: int):
+    """Time the CPU oracle on seq[:prefix]; project to the full fold by n^3."""
+    import oracle
+    oracle.build()
+    s = seq[:prefix]
+    t0 = time.perf_counter()
+    oracle.score(s)
+    dt = time.perf_counter() - t0
+    n = len(seq)
+    scale = (n / prefix) ** 3 if prefix < n else 1.0
+    full_s = dt * scale
+    return full_s, dt
+
+
+def run_reference(a):
+    """--impl reference: the CPU oracle as it stands, on the host cores."""
+    from paper_1307_7820_b300 import metrics, synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    seq = synth.uniform(a.n, 1308)
+    prefix = min(a.n, 3000)
+    for _ in range(a.warmup):
+        cpu_oracle_sample(seq, min(prefix, 1000))
+    times = [cpu_oracle_sample(seq, prefix)[0] for _ in range(a.steps)]
+    ms = 1e3 * statistics.mean(times)
+    value = metrics.cells(a.n) / (ms * 1e-3)
+    sample = (f"each step folds the first {prefix} bases of the n={a.n} input with the cubic oracle "
+              f"(single-threaded C, Eq. 1) and scales its time by (n/{prefix})^3 to one full fold")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic", "config": workload_config(a),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU side
+def main():
+    a = parse_args()
+    if a.impl == "reference":
+        return run_reference(a)
+
+    import torch
+    from paper_1307_7820_b300 import fold, metrics, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+
+    def barrier_sync():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n, q = a.n, a.q
+    seq = synth.uniform(n, 1308)
+    cells = metrics.cells(n)
+    lam = metrics.lookups(n, q)
+
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def make(method):
+        f = fold.Folder(q=q, method=method, device=local)
+        f.option(fold.FOLD_OPT_TIMING, 1)
+        return f
+
+    def device_run(f, steps, warmup, sampler=None):
+        codes = torch.from_numpy(fold.encode_codes(seq)).to(dev)
+        ws = torch.empty(f.workspace_bytes(n), dtype=torch.uint8, device=dev)
+        out = torch.zeros(1, dtype=torch.int32, device=dev)
+        torch.cuda.synchronize()
+        for _ in range(warmup):
+            with torch.cuda.stream(stream):
+                f.score_dev(codes, ws, out, None, stream=stream.cuda_stream)
+        barrier_sync()
+        if sampler:
+            sampler.start()
+        l0 = f.launches
+        step_ms, kern_ms = [], []
+        barrier_sync()
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                f.score_dev(codes, ws, out, None, stream=stream.cuda_stream)
+                e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            kern_ms.append(f.option(fold.FOLD_OPT_KERNEL_NS) / 1e6)
+        barrier_sync()
+        clocks = sampler.stop() if sampler else None
+        launches = f.launches - l0
+        return {"step_ms": step_ms, "kern_ms": kern_ms, "max_pairs": int(out.item()), "launches": launches,
+                "clocks": clocks}
+
+    # ---- headline: two-vector fold, device-resident
+    tv = make("two_vector")
+    sampler = ClockSampler(local)
+    r_tv = device_run(tv, a.steps, a.warmup, sampler)
+    total_ms = max_over_ranks(sum(r_tv["step_ms"]))
+    ms_per_step = total_ms / a.steps
+    value = world * cells / (ms_per_step * 1e-3)
+    kern_ms = statistics.mean(r_tv["kern_ms"])
+
+    # ---- plain comparison kernel, same input and procedure
+    pl = make("plain")
+    r_pl = device_run(pl, max(3, a.steps // 4), a.warmup)
+    pl_ms = statistics.mean(r_pl["step_ms"])
+    assert r_pl["max_pairs"] == r_tv["max_pairs"], "plain and two-vector disagree"
+
+    # ---- end to end through the public host API (pinned staging inside the library)
+    e2e_times = []
+    for k in range(a.warmup + a.steps):
+        barrier_sync()
+        t0 = time.perf_counter()
+        mp = tv.score(seq)
+        dt = time.perf_counter() - t0
+        if k >= a.warmup:
+            e2e_times.append(dt)
+        assert mp == r_tv["max_pairs"]
+    e2e_s = max_over_ranks(statistics.mean(e2e_times))
+    e2e = {"value": world * cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n, "d2h_bytes_per_step": 4,
+           "ms_per_step": e2e_s * 1e3, "api": "fold_score (host string in, max pairs out)"}
+
+    # ---- trace of one fold (optional)
+    if a.trace and rank == 0:
+        tv.option(fold.FOLD_OPT_TRACE, 1)
+        tv.score(seq)
+        np.save(a.trace, fold.fold_trace_copy(tv.ctx))
+        tv.option(fold.FOLD_OPT_TRACE, 0)
+
+    # ---- batched folding: 4096 sequences, log-uniform lengths in [64, 3000]
+    batch = None
+    if not a.no_batch:
+        seqs = synth.batch(4096, 64, 3000, synth.SEED_BASE + 3)
+        tv.batch(seqs[:64])
+        barrier_sync()
+        t0 = time.perf_counter()
+        res = tv.batch(seqs)
+        bt = time.perf_counter() - t0
+        bk = tv.option(fold.FOLD_OPT_KERNEL_NS) / 1e9
+        # one-at-a-time baseline on a 1-in-16 sample, device-timed, scaled to all sequences
+        sample = seqs[::16]
+        loop_s = 0.0
+        for s in sample:
+            codes = torch.from_numpy(fold.encode_codes(s)).to(dev)
+            ws = torch.empty(max(256, tv.workspace_bytes(len(s))), dtype=torch.uint8, device=dev)
+            out = torch.zeros(1, dtype=torch.int32, device=dev)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tv.score_dev(codes, ws, out, None, stream=stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            loop_s += e0.elapsed_time(e1) / 1e3
+        loop_s *= len(seqs) / len(sample)
+        batch = {"sequences": len(seqs), "lengths": "log-uniform [64, 3000]", "seq_per_s_e2e": len(seqs) / bt,
+                 "seq_per_s_kernel": len(seqs) / bk if bk > 0 else None,
+                 "seq_per_s_one_at_a_time": len(seqs) / loop_s,
+                 "speedup_vs_one_at_a_time": (loop_s / bk) if bk > 0 else None,
+                 "one_at_a_time_sample": "device time of every 16th sequence, scaled to 4096",
+                 "total_cells": int(sum(metrics.cells(len(s)) for s in seqs)), "checksum": int(res.sum())}
+
+    # ---- CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if not a.no_cpu and rank == 0 and world == 1:
+        prefix = min(n, 4000)
+        full_s, dt = cpu_oracle_sample(seq, prefix)
+        cpu = {"value": cells / full_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"cubic oracle (single-threaded C, Eq. 1) on the first {prefix} of the {n} bases took "
+                         f"{dt:.2f} s; time scaled by ({n}/{prefix})^3 to one full fold ({full_s:.1f} s)"}
+
+    clocks = r_tv["clocks"] or {}
+    sm_mhz = clocks.get("sm_mhz") or 2032.0
+    peak = metrics.lookup_peak(n_sm, 2032.0)
+    achieved = lam / (kern_ms * 1e-3)
+    roofline = {
+        "bound": "alu", "unit": "Glookups/s", "achieved": achieved / 1e9, "peak": peak / 1e9,
+        "frac": achieved / peak, "traffic": None,
+        "kernel": "fold_kernel<8,two-vector> (persistent)", "kernel_ms": kern_ms,
+        "algorithmic_lookups": lam,
+        "peak_basis": f"{n_sm} SMs x 32 conflict-free shared-memory lookups/clk x 2032 MHz max SM clock",
+        "frac_at_sampled_clock": achieved / metrics.lookup_peak(n_sm, sm_mhz),
+        "hbm_floor_ms": metrics.hbm_bytes(n) / 6479.6e9 * 1e3,
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int16", "data": "synthetic", "config": workload_config(a),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": r_tv["launches"], "clocks": clocks,
+        "plain": {"ms_per_step": pl_ms, "cells_per_s": cells / (pl_ms * 1e-3),
+                  "two_vector_speedup": pl_ms / statistics.mean(r_tv["step_ms"]),
+                  "kernel_ms": statistics.mean(r_pl["kern_ms"])},
+        "batch": batch, "serve": None,
+        "max_pairs": r_tv["max_pairs"],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tv.close()
+    pl.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -71,10 +71,28 @@ enum fold_option {
     FOLD_OPT_Q = 5,           /* read-only: q in use */
     FOLD_OPT_TILE = 6,        /* read-only: tile edge T of the current method */
     FOLD_OPT_LAUNCHES = 7,    /* read-only: kernels launched by this context so far */
-    FOLD_OPT_TEST_DROP_TASK = 8 /* fault injection for tests: 1 = leave the tile (0,1) task out of the
-                                   next single-sequence schedules, so its dependents' bounded waits
-                                   expire and the call returns FOLD_ETIMEOUT; 0 = off (default) */
+    FOLD_OPT_TEST_DROP_TASK = 8, /* fault injection for tests: 1 = leave the tile (0,1) task out of the
+                                    next single-sequence schedules, so its dependents' bounded waits
+                                    expire and the call returns FOLD_ETIMEOUT; 0 = off (default) */
+    FOLD_OPT_TIMING = 9,      /* 1 = record CUDA events around every persistent fold kernel launch */
+    FOLD_OPT_KERNEL_NS = 10,  /* read-only: duration of the last timed fold kernel in ns (waits for it) */
+    FOLD_OPT_TRACE = 11       /* 1 = record per-task timestamps (see fold_trace_copy); 0 = off */
 };
+
+/* One record per task of the last traced persistent launch. */
+typedef struct fold_trace_rec {
+    int32_t worker;     /* global warp index that ran the task */
+    int32_t task;       /* index in the ordered task list */
+    int32_t type;       /* 0 = tile (NEAR), 1 = middle-block chunk (FAR) */
+    int32_t I, J;       /* tile coordinates */
+    int32_t seq;        /* sequence index within the launch */
+    int64_t t_start;    /* %globaltimer ns when the worker took the task */
+    int64_t t_deps;     /* ns when the tiles it reads were published */
+    int64_t t_mid;      /* tile: ns when the partial max over middle blocks was complete;
+                           chunk: ns when its lookups were done */
+    int64_t t_end;      /* ns when its results were published */
+    int64_t t_aux[3];   /* tile only: half of the rows done, all rows done, stores issued */
+} fold_trace_rec;
 
 /* Creates a context on `device`.  q in [2,10] is the vector length of
  * Section 3.1 (0 picks the default, 8); pair_mask as above (must be non-zero
@@ -93,6 +111,10 @@ const char *fold_strerror(int code);
  * option or out-of-range value. */
 int fold_set_option(fold_ctx *ctx, int option, int64_t value);
 int fold_get_option(fold_ctx *ctx, int option, int64_t *value);
+
+/* Copies up to `cap` trace records of the last traced launch (FOLD_OPT_TRACE)
+ * into out and returns how many were written (or a negative status). */
+int64_t fold_trace_copy(fold_ctx *ctx, fold_trace_rec *out, int64_t cap);
 
 /* Copies the R table to host memory: out[(h << (q-1)) | c] = R(h,c) for the
  * (q-1)-bit horizontal vector h and vertical vector c (bit p-1 holds

@@ -137,6 +137,36 @@ int ensure_host(HostBuf &b, size_t bytes) {
     return FOLD_OK;
 }
 
+// Launches the persistent kernel, with CUDA events around it when timing is
+// on and a zeroed per-task trace buffer when tracing is on.
+cudaError_t launch_fold_instrumented(fold_ctx *ctx, FoldParams &p, cudaStream_t st) {
+    cudaError_t e;
+    if (ctx->trace) {
+        size_t bytes = (size_t)std::max(p.ntasks, 1) * kTraceWords * sizeof(long long);
+        if (ensure_buf(ctx->trace_buf, bytes)) return cudaErrorMemoryAllocation;
+        e = cudaMemsetAsync(ctx->trace_buf.ptr, 0, bytes, st);
+        if (e != cudaSuccess) return e;
+        p.trace = reinterpret_cast<long long *>(ctx->trace_buf.ptr);
+        ctx->trace_count = p.ntasks;
+    } else {
+        p.trace = nullptr;
+    }
+    if (ctx->timing) {
+        if (!ctx->ev0) {
+            if ((e = cudaEventCreate(&ctx->ev0)) != cudaSuccess) return e;
+            if ((e = cudaEventCreate(&ctx->ev1)) != cudaSuccess) return e;
+        }
+        if ((e = cudaEventRecord(ctx->ev0, st)) != cudaSuccess) return e;
+    }
+    e = launch_fold(p, ctx->q, ctx->method, grid_for(ctx), st);
+    if (e != cudaSuccess) return e;
+    if (ctx->timing) {
+        if ((e = cudaEventRecord(ctx->ev1, st)) != cudaSuccess) return e;
+        ctx->ev_pending = true;
+    }
+    return cudaSuccess;
+}
+
 // Base letters to codes; returns false on an invalid letter.
 bool encode_seq(const char *seq, int n, uint8_t *out) {
     for (int k = 0; k < n; ++k) {
@@ -204,7 +234,7 @@ int enqueue_single(fold_ctx *ctx, const uint8_t *d_codes, int n, uint8_t *ws, si
         e = launch_pad_codes(d_codes, n, pl.sd[0].Np, ws + pl.off_codes, st);
         if (e != cudaSuccess) return status_from_cuda(e);
         FoldParams p = make_params(ctx, pl, ws, tasks, ntasks, d_sd);
-        e = launch_fold(p, ctx->q, ctx->method, grid_for(ctx), st);
+        e = launch_fold_instrumented(ctx, p, st);
         if (e != cudaSuccess) return status_from_cuda(e);
         ctx->launches += 2;
     }
@@ -295,6 +325,9 @@ void fold_destroy(fold_ctx *ctx) {
     if (ctx->aux.ptr) cudaFree(ctx->aux.ptr);
     if (ctx->dout.ptr) cudaFree(ctx->dout.ptr);
     if (ctx->hstage.ptr) cudaFreeHost(ctx->hstage.ptr);
+    if (ctx->trace_buf.ptr) cudaFree(ctx->trace_buf.ptr);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -322,6 +355,14 @@ int fold_set_option(fold_ctx *ctx, int option, int64_t value) {
             if (value < 0 || value > 1) return FOLD_EINVAL;
             ctx->test_drop_task = (int)value;
             return FOLD_OK;
+        case FOLD_OPT_TIMING:
+            if (value < 0 || value > 1) return FOLD_EINVAL;
+            ctx->timing = (int)value;
+            return FOLD_OK;
+        case FOLD_OPT_TRACE:
+            if (value < 0 || value > 1) return FOLD_EINVAL;
+            ctx->trace = (int)value;
+            return FOLD_OK;
     }
     return FOLD_EINVAL;
 }
@@ -337,8 +378,50 @@ int fold_get_option(fold_ctx *ctx, int option, int64_t *value) {
         case FOLD_OPT_TILE: *value = tile_of(ctx->q, ctx->method); return FOLD_OK;
         case FOLD_OPT_LAUNCHES: *value = (int64_t)ctx->launches; return FOLD_OK;
         case FOLD_OPT_TEST_DROP_TASK: *value = ctx->test_drop_task; return FOLD_OK;
+        case FOLD_OPT_TIMING: *value = ctx->timing; return FOLD_OK;
+        case FOLD_OPT_TRACE: *value = ctx->trace; return FOLD_OK;
+        case FOLD_OPT_KERNEL_NS: {
+            if (!ctx->ev_pending) { *value = 0; return FOLD_OK; }
+            float ms = 0.f;
+            cudaError_t e = cudaEventSynchronize(ctx->ev1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+            if (e != cudaSuccess) return status_from_cuda(e);
+            *value = (int64_t)((double)ms * 1e6);
+            return FOLD_OK;
+        }
     }
     return FOLD_EINVAL;
+}
+
+int64_t fold_trace_copy(fold_ctx *ctx, fold_trace_rec *out, int64_t cap) {
+    if (!ctx || (!out && cap > 0) || cap < 0) return -FOLD_EINVAL;
+    if (!ctx->trace_buf.ptr || ctx->trace_count == 0) return 0;
+    cudaSetDevice(ctx->device);
+    int64_t count = std::min<int64_t>(cap, ctx->trace_count);
+    std::vector<long long> h((size_t)count * kTraceWords);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && count)
+        e = cudaMemcpy(h.data(), ctx->trace_buf.ptr, (size_t)count * kTraceWords * sizeof(long long),
+                       cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return -status_from_cuda(e);
+    for (int64_t k = 0; k < count; ++k) {
+        const long long *r = &h[(size_t)k * kTraceWords];
+        fold_trace_rec &o = out[k];
+        o.worker = (int32_t)(r[0] >> 32);
+        o.task = (int32_t)(r[0] & 0xffffffffLL);
+        o.type = (int32_t)(r[1] >> 32);
+        o.seq = (int32_t)(r[1] & 0xffffffffLL);
+        o.I = (int32_t)(r[2] >> 32);
+        o.J = (int32_t)(r[2] & 0xffffffffLL);
+        o.t_start = r[3];
+        o.t_deps = r[4];
+        o.t_mid = r[5];
+        o.t_end = r[6];
+        o.t_aux[0] = r[7];
+        o.t_aux[1] = r[8];
+        o.t_aux[2] = r[9];
+    }
+    return count;
 }
 
 int fold_rtable(fold_ctx *ctx, uint8_t *out, int64_t cap) {
@@ -437,7 +520,7 @@ int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int3
     if (e != cudaSuccess) return status_from_cuda(e);
     FoldParams p = make_params(ctx, pl, ws, d_tasks, (int)tv.size(), d_sd);
     if (!tv.empty()) {
-        e = launch_fold(p, ctx->q, ctx->method, grid_for(ctx), st);
+        e = launch_fold_instrumented(ctx, p, st);
         if (e != cudaSuccess) return status_from_cuda(e);
         ctx->launches += 1;
     }

@@ -54,6 +54,13 @@ struct fold_ctx {
     fold::DevBuf ws, aux, dout;
     fold::HostBuf hstage;
     unsigned long long launches = 0;
+    // kernel timing (FOLD_OPT_TIMING) and task tracing (FOLD_OPT_TRACE)
+    int timing = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool ev_pending = false;
+    int trace = 0;
+    fold::DevBuf trace_buf;
+    int trace_count = 0;
     fold::ServeState *serve = nullptr;
 };
 
@@ -64,5 +71,6 @@ FoldParams make_params(const fold_ctx *ctx, const Plan &pl, uint8_t *ws, const i
 int grid_for(fold_ctx *ctx);
 int kc_auto(int NT);
 int status_from_cuda(cudaError_t e);
+cudaError_t launch_fold_instrumented(fold_ctx *ctx, FoldParams &p, cudaStream_t st);
 bool encode_seq(const char *seq, int n, uint8_t *out);
 }  // namespace fold

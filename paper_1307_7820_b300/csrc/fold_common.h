@@ -17,6 +17,7 @@ constexpr int kColOff = 7;                      // Dcol offset: D(i,j) at Dcol[j
 constexpr int kRing = 8;                        // P (far partial max) ring depth in tile diagonals
 constexpr int kNeg16 = -32768;                  // int16 "minus infinity" for the row closure
 constexpr int kPadCode = 4;                     // padding base: pairs with nothing
+constexpr int kTraceWords = 10;                 // 64-bit words per task trace record
 
 enum Method : int { kTwoVector = 0, kPlain = 1 };
 enum TaskType : int { kTaskNear = 0, kTaskFar = 1 };
@@ -71,6 +72,7 @@ struct FoldParams {
     const uint8_t *rtab;      // R table in the kernel's smem layout
     unsigned long long pair64;  // bit (8x+y) = b(x,y)
     long long timeout_ns;     // bound on every device-side wait
+    long long *trace;         // optional: kTraceWords words per task (see fold_trace_rec), or nullptr
 };
 
 // error word values written by the kernel

@@ -59,10 +59,10 @@ static __device__ __noinline__ bool wait_geq_impl(const int *p, int target, int 
     if (lane == 0) {
         if (ld_acquire(p) < target) {
             unsigned long long t0 = gtimer();
-            unsigned ns = 64;
+            unsigned ns = 32;
             for (;;) {
                 __nanosleep(ns);
-                if (ns < 2048) ns <<= 1;
+                if (ns < 256) ns <<= 1;
                 if (ld_acquire(p) >= target) break;
                 if (*(volatile int *)error != 0) { ok = 0; break; }
                 if ((long long)(gtimer() - t0) > timeout_ns) {
@@ -99,13 +99,25 @@ template <int Q, int M>
 struct __align__(16) WarpScratch {
     static constexpr int T = Cfg<Q, M>::T;
     static constexpr int G = Cfg<Q, M>::G;
-    int2 rf[G][32];                 // far staging (two-vector): (A, h-row byte offset)
-    alignas(16) int16_t rows[32][32];  // far staging (plain): row strips (uint4 access)
-    int16_t diag[T][T + 2];         // diagonal tile (I,I) rows
-    uint32_t drf[T][G];             // diagonal tile row features
-    alignas(16) int16_t y[32];      // closure exchange (read back as uint4)
-    int16_t left[T + 2];            // D(IT+m, JT-1)
-    int16_t tile[T][T + 1];         // output tile (transposed store)
+    static constexpr bool PL = (M == kPlain);
+    static constexpr int LR = PL ? 32 : 1;         // plain: late-block row strips
+    static constexpr int LF = PL ? 1 : T;          // two-vector: late-block row features
+    int2 rf[G][32];                    // FAR staging (two-vector): (A, h-row byte offset)
+    alignas(16) int16_t rows[LR][32];  // FAR staging (plain): row strips (uint4 access)
+    alignas(16) int16_t lrow[2][LR][32];  // NEAR late blocks (plain): rows of tiles (I,J-1), (I,I+1)
+    alignas(16) uint32_t colpk[PL ? 16 : 1][32];  // NEAR (plain): (D(IT+2m+1,j), D(IT+2m+2,j)) pairs, per lane
+    uint32_t lrf[2][LF][G];            // NEAR late blocks (two-vector): row features of (I,J-1), (I,I+1)
+    uint32_t cbc[G + 1][32];           // NEAR (two-vector): (base << 16 | bits) of the lane's column groups;
+                                       // row G takes the stores of rows that complete no group
+    static constexpr int DS = PL ? 40 : T + 2;   // row stride (plain reads rows as uint4)
+    alignas(16) int16_t diag[T][DS];   // diagonal tile (I,I) rows
+    uint32_t drf[T][G];                // diagonal tile row features
+    int16_t pm[T][32];                 // far partial max of each row (lane = column)
+    alignas(16) int16_t y[2][32];      // closure exchange, double-buffered (read back as uint4)
+    int16_t left[T + 2];               // D(IT+m, JT-1)
+    uint8_t rcode[32];                 // codes of the tile's rows
+    int16_t tile[T + 1][33];           // output tile; row T holds D((I+1)T, j); 33 columns so every lane's
+                                       // index (also lanes >= T) stays inside the array
 };
 
 // every vector-accessed member must sit on a 16-byte boundary
@@ -114,6 +126,8 @@ struct ScratchChecks {
     using WS = WarpScratch<Q, M>;
     static_assert(offsetof(WS, y) % 16 == 0, "y must be 16-byte aligned");
     static_assert(offsetof(WS, rows) % 16 == 0, "rows must be 16-byte aligned");
+    static_assert(offsetof(WS, lrow) % 16 == 0, "lrow must be 16-byte aligned");
+    static_assert(M != kPlain || (offsetof(WS, diag) % 16 == 0 && (WS::DS * 2) % 16 == 0), "diag rows 16-byte aligned");
     static_assert(sizeof(WarpScratch<Q, M>) % 16 == 0, "scratch stride must keep 16-byte alignment");
     static constexpr bool ok = true;
 };
@@ -213,24 +227,39 @@ static __device__ __forceinline__ void far_block_plain(const FoldParams &P, cons
     __syncwarp();
 }
 
+// max of N values as a balanced tree (short dependency chains)
+template <int N>
+__device__ __forceinline__ int tree_max(int (&v)[N]) {
+    int w[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) w[k] = v[k];
+#pragma unroll
+    for (int span = 1; span < N; span *= 2) {
+#pragma unroll
+        for (int k = 0; k + span < N; k += 2 * span) w[k] = max(w[k], w[k + span]);
+    }
+    return w[0];
+}
+
 static __device__ __forceinline__ int hmax2(unsigned a) {
     return max((int)(short)(a & 0xffffu), (int)(short)(a >> 16));
 }
 
 // ---------------------------------------------------------------- FAR task
 template <int Q, int M>
-__device__ void run_far(const FoldParams &P, const SeqDesc &sd, int I, int J, int Ka, int Kb,
-                        WarpScratch<Q, M> &ws, const uint8_t *Rs, int lane) {
+__device__ __forceinline__ long long run_far(const FoldParams &P, const SeqDesc &sd, int I, int J, int Ka, int Kb,
+                        WarpScratch<Q, M> &ws, const uint8_t *Rs, int lane, long long *tdeps) {
     constexpr int T = Cfg<Q, M>::T;
     const int NT = sd.NT;
     int *flags = P.flags + sd.flag_off;
     if (Kb < Ka || Ka <= I || Kb >= J) {
         if (lane == 0) atomicCAS(P.error, 0, kErrBadTask);
-        return;
+        return 0;
     }
-    if (!warp_wait_geq(flags + I * NT + Kb, 1, P, lane)) return;
-    if (!warp_wait_geq(flags + Ka * NT + J, 1, P, lane)) return;
-    if (J - I >= kRing && !warp_wait_geq(flags + I * NT + (J - kRing), 1, P, lane)) return;
+    if (!warp_wait_geq(flags + I * NT + Kb, 1, P, lane)) return 0;
+    if (!warp_wait_geq(flags + Ka * NT + J, 1, P, lane)) return 0;
+    if (J - I >= kRing && !warp_wait_geq(flags + I * NT + (J - kRing), 1, P, lane)) return 0;
+    if (P.trace) tdeps[0] = (long long)gtimer();
     int m[T];
     if constexpr (M == kTwoVector) {
 #pragma unroll
@@ -244,6 +273,7 @@ __device__ void run_far(const FoldParams &P, const SeqDesc &sd, int I, int J, in
 #pragma unroll
         for (int r = 0; r < T; ++r) m[r] = hmax2(mp[r]);
     }
+    const long long tdone = P.trace ? (long long)gtimer() : 0;
     int *slot = P.pring + sd.p_off + ((size_t)((J - I) % kRing) * NT + I) * (T * T);
     if (lane < T) {
 #pragma unroll
@@ -253,12 +283,13 @@ __device__ void run_far(const FoldParams &P, const SeqDesc &sd, int I, int J, in
     __threadfence();
     __syncwarp();
     if (lane == 0) atomicAdd(P.cnt + sd.cnt_off + I * NT + J, 1);
+    return tdone;
 }
 
 // ---------------------------------------------------------------- NEAR task
 template <int Q, int M>
-__device__ void run_near(const FoldParams &P, const SeqDesc &sd, int I, int J, int nfar, WarpScratch<Q, M> &ws,
-                         const uint8_t *Rs, int lane) {
+__device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc &sd, int I, int J, int nfar,
+                                              WarpScratch<Q, M> &ws, const uint8_t *Rs, int lane, long long *tdeps) {
     using C = Cfg<Q, M>;
     constexpr int T = C::T, G = C::G;
     constexpr bool TV = (M == kTwoVector);
@@ -272,192 +303,401 @@ __device__ void run_near(const FoldParams &P, const SeqDesc &sd, int I, int J, i
     int16_t *Drow = P.drow + sd.drow_off;
     int16_t *Dcol = P.dcol + sd.dcol_off;
     const uint8_t *codes = P.codes + sd.code_off;
+    const uint32_t *RF = P.rf + sd.rf_off;
+    const uint32_t *CF = P.cf + sd.cf_off;
+    const int NG = TV ? Np / Q : 1;
+    const bool lateA = t >= 2;   // middle block K = J-1: rows of tile (I,J-1) x column of tile (J-1,J)
+    const bool lateB = t >= 3;   // middle block K = I+1: rows of tile (I,I+1) x column of tile (I+1,J)
 
+    // ---- inputs from tiles finished long before the neighbours, all loads in flight at once
+    unsigned Wp[16];           // packed W[c'][c] = D(JT+c'+1, j) for c' < c, sentinel otherwise
+    int lB[2][G], lC[2][G];    // late-block column features (two-vector)
+    unsigned lcol[2][16];      // late-block columns as packed pairs (plain)
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+#pragma unroll
+        for (int gl = 0; gl < G; ++gl) { lB[k][gl] = 0; lC[k][gl] = 0; }
+#pragma unroll
+        for (int v = 0; v < 16; ++v) lcol[k][v] = 0;
+    }
+    if (valid) ws.rcode[c] = codes[IT + c];
     if (t >= 1) {
-        if (!warp_wait_geq(flags + I * NT + (J - 1), 1, P, lane)) return;
-        if (!warp_wait_geq(flags + (I + 1) * NT + J, 1, P, lane)) return;
-    }
-    // far partial max: late blocks K = J-1 and K = I+1 here, the rest from FAR chunks
-    int m[T];
-    if constexpr (TV) {
+        if (!warp_wait_geq(flags + I * NT + I, 1, P, lane)) return 0;
+        if (!warp_wait_geq(flags + J * NT + J, 1, P, lane)) return 0;
+        if (lateA && !warp_wait_geq(flags + (J - 1) * NT + J, 1, P, lane)) return 0;
+        if (lateB && !warp_wait_geq(flags + I * NT + (I + 1), 1, P, lane)) return 0;
+        int16_t dv[T];
 #pragma unroll
-        for (int r = 0; r < T; ++r) m[r] = 0;
-        if (t >= 2) far_block_tv<Q>(P, sd, I, J, J - 1, m, ws, Rs, lane);
-        if (t >= 3) far_block_tv<Q>(P, sd, I, J, I + 1, m, ws, Rs, lane);
-    } else {
-        unsigned mp[T];
-#pragma unroll
-        for (int r = 0; r < T; ++r) mp[r] = 0;
-        if (t >= 2) far_block_plain(P, sd, I, J, J - 1, mp, ws, lane);
-        if (t >= 3) far_block_plain(P, sd, I, J, I + 1, mp, ws, lane);
-#pragma unroll
-        for (int r = 0; r < T; ++r) m[r] = hmax2(mp[r]);
-    }
-    if (nfar > 0) {
-        if (!warp_wait_geq(P.cnt + sd.cnt_off + I * NT + J, nfar, P, lane)) return;
-        int *slot = P.pring + sd.p_off + ((size_t)(t % kRing) * NT + I) * (T * T);
-        if (valid) {
-#pragma unroll
-            for (int r = 0; r < T; ++r) {
-                m[r] = max(m[r], __ldcg(slot + r * T + c));
-                __stcg(slot + r * T + c, 0);   // the ring slot is reused by tile (I, J+kRing)
-            }
-        }
-    }
-
-    // ---- stage inputs
-    const int sj = valid ? (int)codes[j] : kPadCode;
-    int colv[T + 1];           // colv[r] = D(IT+r, j) once row r is done; colv[T] = D((I+1)T, j)
-#pragma unroll
-    for (int r = 0; r <= T; ++r) colv[r] = 0;
-    if (t >= 1 && valid && (I + 1) * T < Np) colv[T] = ldcg16(Drow + (size_t)((I + 1) * T) * Np + j);
-    unsigned Wp[16];           // packed W[c'][c] pairs (off-diagonal tiles)
-    if (t >= 1) {
-        // diagonal tile (I,I): rows for the residual splits (two-vector) or all column-side splits (plain)
-        for (int r = 0; r < T; ++r)
-            if (valid) ws.diag[r][c] = (int16_t)ldcg16(Drow + (size_t)(IT + r) * Np + IT + c);
-        if constexpr (TV) {
-            const int NG = Np / Q;
-            for (int r = 0; r < T; ++r)
-                if (c < G) ws.drf[r][c] = __ldcg(P.rf + sd.rf_off + (size_t)(IT + r) * NG + I * G + c);
-        }
-        // left column D(IT+m, JT-1), m = 1..T (pair term of lane 0); rows below JT-1 are 0
-        if (valid) {
-            int row = IT + 1 + c;   // m = c + 1
-            int v = 0;
-            if (row <= JT - 1 && row < Np) v = ldcg16(Dcol + (size_t)(JT - 1) * PC + row + kColOff);
-            ws.left[c + 1] = (int16_t)v;
-        }
-        // W column: D(JT+c'+1, j) for c' < c, sentinel otherwise
+        for (int r = 0; r < T; ++r) dv[r] = valid ? __ldcg(Drow + (size_t)(IT + r) * Np + IT + c) : (int16_t)0;
 #pragma unroll
         for (int mm = 0; mm < 16; ++mm) {
+            const int c0 = 2 * mm, c1 = 2 * mm + 1;
             int w0 = kNeg16, w1 = kNeg16;
-            int c0 = 2 * mm, c1 = 2 * mm + 1;
             if (valid && c0 < c) w0 = ldcg16(Dcol + (size_t)j * PC + JT + c0 + 1 + kColOff);
             if (valid && c1 < c) w1 = ldcg16(Dcol + (size_t)j * PC + JT + c1 + 1 + kColOff);
             Wp[mm] = (unsigned)(w0 & 0xffff) | ((unsigned)w1 << 16);
         }
+        if constexpr (TV) {
+            constexpr int E = (T * G + 31) / 32;   // row features of (I,I) and (I,I+1), spread over the warp
+            uint32_t fv[E], fb[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int idx = e * 32 + lane;
+                const bool in = idx < T * G;
+                const size_t row = (size_t)(IT + idx / G) * NG;
+                fv[e] = in ? __ldcg(RF + row + I * G + idx % G) : 0u;
+                fb[e] = (in && lateB) ? __ldcg(RF + row + (I + 1) * G + idx % G) : 0u;
+            }
+            if (lateA && valid) {
+#pragma unroll
+                for (int gl = 0; gl < G; ++gl) {
+                    const uint32_t cf = __ldcg(CF + (size_t)((J - 1) * G + gl) * Np + j);
+                    lB[0][gl] = (int)(cf >> 16);
+                    lC[0][gl] = (int)(cf & C::BMASK);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int idx = e * 32 + lane;
+                if (idx < T * G) {
+                    ws.drf[idx / G][idx % G] = fv[e];
+                    ws.lrf[1][idx / G][idx % G] = fb[e];
+                }
+            }
+        } else {
+            if (lateB) {   // row strip of tile (I, I+1), row IT+lane
+                const uint4 *src = reinterpret_cast<const uint4 *>(Drow + (size_t)(IT + lane) * Np + (I + 1) * T);
+                uint4 *dst = reinterpret_cast<uint4 *>(&ws.lrow[1][lane][0]);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) dst[v] = __ldcg(src + v);
+            }
+            if (lateA) {   // column j of tile (J-1, J): rows (J-1)T+1 .. JT
+                const uint4 *cs = reinterpret_cast<const uint4 *>(Dcol + (size_t)j * PC + (J - 1) * T + 1 + kColOff);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    uint4 w = __ldcg(cs + v);
+                    lcol[0][4 * v] = w.x; lcol[0][4 * v + 1] = w.y; lcol[0][4 * v + 2] = w.z; lcol[0][4 * v + 3] = w.w;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < T; ++r)
+            if (valid) ws.diag[r][c] = dv[r];
     } else {
 #pragma unroll
         for (int mm = 0; mm < 16; ++mm) Wp[mm] = 0;
     }
+
+    // ---- the two neighbours that finish last
+    if (t >= 1) {
+        if (!warp_wait_geq(flags + I * NT + (J - 1), 1, P, lane)) return 0;
+        if (!warp_wait_geq(flags + (I + 1) * NT + J, 1, P, lane)) return 0;
+    }
+    if (P.trace) tdeps[0] = (long long)gtimer();
+    int colT = 0;              // D((I+1)T, j): row 0 of tile (I+1, J)
+    int leftv = 0;             // D(IT+1+c, JT-1): left column for lane 0's pair term
+    if (t >= 1 && valid) {
+        if ((I + 1) * T < Np) colT = ldcg16(Drow + (size_t)((I + 1) * T) * Np + j);
+        const int row = IT + 1 + c;
+        if (row <= JT - 1 && row < Np) leftv = ldcg16(Dcol + (size_t)(JT - 1) * PC + row + kColOff);
+    }
+    if constexpr (TV) {
+        if (lateA) {
+            constexpr int E = (T * G + 31) / 32;
+            uint32_t fa[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int idx = e * 32 + lane;
+                fa[e] = idx < T * G ? __ldcg(RF + (size_t)(IT + idx / G) * NG + (J - 1) * G + idx % G) : 0u;
+            }
+            if (lateB && valid) {
+#pragma unroll
+                for (int gl = 0; gl < G; ++gl) {
+                    const uint32_t cf = __ldcg(CF + (size_t)((I + 1) * G + gl) * Np + j);
+                    lB[1][gl] = (int)(cf >> 16);
+                    lC[1][gl] = (int)(cf & C::BMASK);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int idx = e * 32 + lane;
+                if (idx < T * G) ws.lrf[0][idx / G][idx % G] = fa[e];
+            }
+        }
+    } else {
+        if (lateA) {   // row strip of tile (I, J-1), row IT+lane
+            const uint4 *src = reinterpret_cast<const uint4 *>(Drow + (size_t)(IT + lane) * Np + (J - 1) * T);
+            uint4 *dst = reinterpret_cast<uint4 *>(&ws.lrow[0][lane][0]);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) dst[v] = __ldcg(src + v);
+        }
+        if (lateB) {   // column j of tile (I+1, J): rows (I+1)T+1 .. (I+2)T
+            const uint4 *cs = reinterpret_cast<const uint4 *>(Dcol + (size_t)j * PC + (I + 1) * T + 1 + kColOff);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                uint4 w = __ldcg(cs + v);
+                lcol[1][4 * v] = w.x; lcol[1][4 * v + 1] = w.y; lcol[1][4 * v + 2] = w.z; lcol[1][4 * v + 3] = w.w;
+            }
+        }
+    }
+    // an absent late block gets neutral data (zero features / zero rows), so the row loop can
+    // evaluate both blocks unconditionally
+    if constexpr (TV) {
+        if (!lateA) {
+            constexpr int E = (T * G + 31) / 32;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int idx = e * 32 + lane;
+                if (idx < T * G) ws.lrf[0][idx / G][idx % G] = 0u;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (k == 0 ? !lateA : !lateB) {
+                uint4 *dst = reinterpret_cast<uint4 *>(&ws.lrow[k][lane][0]);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) dst[v] = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+    }
+    // partial max of the FAR chunks (middle blocks I+2 .. J-2), staged per row in shared memory
+    if (nfar > 0) {
+        if (!warp_wait_geq(P.cnt + sd.cnt_off + I * NT + J, nfar, P, lane)) return 0;
+        int *slot = P.pring + sd.p_off + ((size_t)(t % kRing) * NT + I) * (T * T);
+        if (valid) {
+            int pv[T];
+#pragma unroll
+            for (int r = 0; r < T; ++r) pv[r] = __ldcg(slot + r * T + c);
+#pragma unroll
+            for (int r = 0; r < T; ++r) {
+                ws.pm[r][c] = (int16_t)pv[r];
+                __stcg(slot + r * T + c, 0);   // ring slot reused by tile (I, J+kRing)
+            }
+        }
+    } else if (valid) {
+#pragma unroll
+        for (int r = 0; r < T; ++r) ws.pm[r][c] = 0;
+    }
+    const long long tfar = P.trace ? (long long)gtimer() : 0;
+
+    const int sj = valid ? (int)codes[j] : kPadCode;
+    if (valid) {
+        ws.left[c + 1] = (int16_t)leftv;
+        ws.tile[T][c] = (int16_t)colT;
+    }
     if (c == 0) ws.left[0] = 0;
+    if constexpr (!TV) {
+        // column pairs (D(IT+2m+1,j), D(IT+2m+2,j)); rows not yet computed hold the sentinel
+#pragma unroll
+        for (int mm = 0; mm < 16; ++mm)
+            ws.colpk[mm][c] = (mm == 15) ? ((unsigned)(kNeg16 & 0xffff) | ((unsigned)colT << 16))
+                                         : ((unsigned)(kNeg16 & 0xffff) | ((unsigned)(kNeg16 & 0xffff) << 16));
+    }
     __syncwarp();
 
     const unsigned long long pair64 = P.pair64;
-    int below = colv[T];       // D(i+1, j) for the current row i
     unsigned vhist = 0;        // vertical differences, newest in bit 0
-    int colB[G], colC[G];
-#pragma unroll
-    for (int gl = 0; gl < G; ++gl) { colB[gl] = 0; colC[gl] = 0; }
-    const int NG = TV ? Np / Q : 1;
 
-#pragma unroll
-    for (int r = T - 1; r >= 0; --r) {
-        const int i = IT + r;
-        const int si = (int)codes[i];
-        const unsigned rowbits = (unsigned)(pair64 >> (8 * si)) & 0xffu;
-        // D(i+1, j-1): lane c-1's previous row; lane 0 reads the left column
-        int bl = __shfl_up_sync(FULL, below, 1);
-        if (c == 0) bl = (r == T - 1) ? ((t >= 1 && J >= 1) ? (int)ws.left[T] : 0) : (int)ws.left[r + 1];
-        const int pb = (int)((rowbits >> sj) & 1u);
-        int y;
-        if (t == 0) {
-            y = (c > r) ? pb + bl : (c == r ? 0 : kNeg16);
-        } else {
-            y = max(pb + bl, m[r]);
-            if constexpr (TV) {
-                const int ce = (r + Q - 1) / Q * Q;
-                // residual splits k in [i+1, IT+ce]: D(i,k-1) from tile (I,I), D(k,j) from this column
-#pragma unroll
-                for (int kk = r + 1; kk <= ce; ++kk) y = max(y, (int)ws.diag[r][kk - 1] + colv[kk]);
-                // full groups of tile column I with g*q >= i (Eq. 3)
-#pragma unroll
-                for (int gl = ce / Q; gl < G; ++gl) {
-                    uint32_t f = ws.drf[r][gl];
-                    int v = rlookup<Q>(Rs, hrow_offset<Q>((int)(f & C::BMASK)), colC[gl]);
-                    y = max(y, (int)(f >> 16) + colB[gl] + v);
-                }
-            } else {
-                // every split with D(k,j) in this tile column: k in [i+1, IT+T]
-#pragma unroll
-                for (int kk = r + 1; kk <= T; ++kk) y = max(y, (int)ws.diag[r][kk - 1] + colv[kk]);
-            }
-        }
-        if (!valid) y = kNeg16;
-        // closure over the row: D_c = max(Y_c, max_{c'<c} Y_c' + W[c'][c])
-        ws.y[c] = (int16_t)y;
-        __syncwarp();
-        unsigned acc = 0;
-        const uint4 *yp = reinterpret_cast<const uint4 *>(ws.y);
-        if (t == 0) {
-            // W from this (diagonal) tile's own column: D(IT+c'+1, j), valid for rows already done
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                uint4 a = yp[v];
-                unsigned aw[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    int c0 = 8 * v + 2 * e, c1 = c0 + 1;
-                    int w0 = (c0 < c && c0 + 1 <= T) ? colv[c0 + 1 <= T ? c0 + 1 : T] : kNeg16;
-                    int w1 = (c1 < c && c1 + 1 <= T) ? colv[c1 + 1 <= T ? c1 + 1 : T] : kNeg16;
-                    unsigned wp = (unsigned)(w0 & 0xffff) | ((unsigned)w1 << 16);
-                    acc = __viaddmax_s16x2(aw[e], wp, acc);
-                }
-            }
-        } else {
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                uint4 a = yp[v];
-                acc = __viaddmax_s16x2(a.x, Wp[4 * v + 0], acc);
-                acc = __viaddmax_s16x2(a.y, Wp[4 * v + 1], acc);
-                acc = __viaddmax_s16x2(a.z, Wp[4 * v + 2], acc);
-                acc = __viaddmax_s16x2(a.w, Wp[4 * v + 3], acc);
-            }
-        }
-        __syncwarp();
-        int d = max(y, hmax2(acc));
-        if (t == 0 && c < r) d = 0;
-        if (!valid) d = 0;
-        // ---- features
-        const int vb = d - colv[r + 1];   // vertical difference D(i,j) - D(i+1,j)
-        vhist = (vhist << 1) | (unsigned)(vb & 1);
-        colv[r] = d;
-        below = d;
-        if (valid) ws.tile[r][c] = (int16_t)d;
+    // terms of row rr that do not depend on row rr+1 (computed while row rr+1 closes); branch-free:
+    // every candidate is evaluated with in-range indices and the invalid ones are masked
+    auto old_terms = [&](int rr) -> int {
         if constexpr (TV) {
-            if (r >= 1 && (r - 1) % Q == 0) {
-                const int gl = (r - 1) / Q;   // group rows gl*q+1 .. gl*q+q complete
-                colB[gl] = d;
-                colC[gl] = (int)(vhist & C::BMASK);
-                if (valid) P.cf[sd.cf_off + (size_t)(I * G + gl) * Np + j] = ((uint32_t)d << 16) | (vhist & C::BMASK);
+            constexpr int NC = 1 + 2 * G + (Q > 2 ? Q - 2 : 0) + G;
+            int cand[NC];
+            int k = 0;
+            cand[k++] = (int)ws.pm[rr][c];
+#pragma unroll
+            for (int kb = 0; kb < 2; ++kb) {
+#pragma unroll
+                for (int gl = 0; gl < G; ++gl) {
+                    const uint32_t f = ws.lrf[kb][rr][gl];
+                    const int v = rlookup<Q>(Rs, hrow_offset<Q>((int)(f & C::BMASK)), lC[kb][gl]);
+                    cand[k++] = (int)(f >> 16) + lB[kb][gl] + v;
+                }
             }
+            const int ce = (rr + Q - 1) / Q * Q;
+            // residual splits k in [i+2, IT+ce] (k = i+1 is the fresh D(i+1,j) term)
+#pragma unroll
+            for (int e = 0; e < Q - 2; ++e) {
+                const int kk = rr + 2 + e;
+                const int ix = min(kk, T);
+                const int v = (int)ws.diag[rr][ix - 1] + (int)ws.tile[ix][c];
+                cand[k++] = (kk <= ce) ? v : kNeg16;
+            }
+            // full groups of tile column I completed before row rr+1 (g*q > rr)
+#pragma unroll
+            for (int gl = 0; gl < G; ++gl) {
+                const uint32_t f = ws.drf[rr][gl];
+                const uint32_t cb = ws.cbc[gl][c];
+                const int v = rlookup<Q>(Rs, hrow_offset<Q>((int)(f & C::BMASK)), (int)(cb & C::BMASK));
+                cand[k++] = (gl * Q > rr) ? (int)(f >> 16) + (int)(cb >> 16) + v : kNeg16;
+            }
+            return tree_max<NC>(cand);
+        } else {
+            unsigned acc[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] = 0;
+#pragma unroll
+            for (int kb = 0; kb < 2; ++kb) {
+                const uint4 *rw = reinterpret_cast<const uint4 *>(&ws.lrow[kb][rr][0]);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const uint4 a = rw[v];
+                    acc[4 * kb + 0] = __viaddmax_s16x2(a.x, lcol[kb][4 * v + 0], acc[4 * kb + 0]);
+                    acc[4 * kb + 1] = __viaddmax_s16x2(a.y, lcol[kb][4 * v + 1], acc[4 * kb + 1]);
+                    acc[4 * kb + 2] = __viaddmax_s16x2(a.z, lcol[kb][4 * v + 2], acc[4 * kb + 2]);
+                    acc[4 * kb + 3] = __viaddmax_s16x2(a.w, lcol[kb][4 * v + 3], acc[4 * kb + 3]);
+                }
+            }
+            // every split with D(k,j) in this tile column: rows not yet done hold the sentinel
+            unsigned acc2[4] = {0u, 0u, 0u, 0u};
+            const uint4 *dw = reinterpret_cast<const uint4 *>(&ws.diag[rr][0]);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const uint4 a = dw[v];
+                acc2[0] = __viaddmax_s16x2(a.x, ws.colpk[4 * v + 0][c], acc2[0]);
+                acc2[1] = __viaddmax_s16x2(a.y, ws.colpk[4 * v + 1][c], acc2[1]);
+                acc2[2] = __viaddmax_s16x2(a.z, ws.colpk[4 * v + 2][c], acc2[2]);
+                acc2[3] = __viaddmax_s16x2(a.w, ws.colpk[4 * v + 3][c], acc2[3]);
+            }
+            const unsigned m4 = __vmaxs2(__vmaxs2(__vmaxs2(acc[0], acc[1]), __vmaxs2(acc[2], acc[3])),
+                                         __vmaxs2(__vmaxs2(acc[4], acc[5]), __vmaxs2(acc[6], acc[7])));
+            const unsigned m2 = __vmaxs2(__vmaxs2(acc2[0], acc2[1]), __vmaxs2(acc2[2], acc2[3]));
+            return max((int)ws.pm[rr][c], hmax2(__vmaxs2(m4, m2)));
+        }
+    };
+
+    // publishes row r (value d of this lane's column): tile copy, row-major store, vertical and
+    // horizontal difference vectors
+    auto publish = [&](int r, int d, int below_prev) {
+        ws.tile[r][c] = (int16_t)d;
+        if (T == 32 || valid) Drow[(size_t)(IT + r) * Np + j] = (int16_t)d;
+        const int vb = d - below_prev;   // vertical difference D(i,j) - D(i+1,j)
+        vhist = (vhist << 1) | (unsigned)(vb & 1);
+        if constexpr (TV) {
+            const bool done = r >= 1 && (r - 1) % Q == 0;   // group rows gl*q+1 .. gl*q+q complete
+            const int gl = max(r - 1, 0) / Q;
+            const uint32_t cb = ((uint32_t)d << 16) | (vhist & C::BMASK);
+            ws.cbc[done ? gl : G][c] = cb;
+            if (done && valid) P.cf[sd.cf_off + (size_t)(I * G + gl) * Np + j] = cb;
             const int dl = __shfl_up_sync(FULL, d, 1);
             const unsigned hb = __ballot_sync(FULL, (d - dl) == 1);
             const int a = __shfl_sync(FULL, d, (c < G) ? c * Q : 0);
             if (c < G)
-                P.rf[sd.rf_off + (size_t)i * NG + J * G + c] = ((uint32_t)a << 16) | ((hb >> (c * Q + 1)) & C::BMASK);
+                P.rf[sd.rf_off + (size_t)(IT + r) * NG + J * G + c] = ((uint32_t)a << 16) | ((hb >> (c * Q + 1)) & C::BMASK);
+        } else {
+            // row r joins the column pairs used by the rows above
+            const int mm = max(r - 1, 0) >> 1;
+            const uint32_t w = ws.colpk[mm][c];
+            const uint32_t w2 = (r & 1) ? ((w & 0xffff0000u) | ((uint32_t)d & 0xffffu)) : ((w & 0xffffu) | ((uint32_t)d << 16));
+            ws.colpk[mm][c] = (r >= 1) ? w2 : w;
+        }
+    };
+
+    int below = colT;          // D(i+1, j)
+    if (t == 0) {
+        // diagonal tile: every split lies in this tile, so the closure alone covers them; W is this
+        // tile's own column D(IT+c'+1, j), valid for r <= c' < c
+#pragma unroll 1
+        for (int r = T - 1; r >= 0; --r) {
+            if (r == T / 2 && P.trace) tdeps[1] = (long long)gtimer();
+            const int si = (int)ws.rcode[r];
+            const int pb = (int)((((unsigned)(pair64 >> (8 * si))) >> sj) & 1u);
+            int bl = __shfl_up_sync(FULL, below, 1);
+            bl = (c == 0) ? 0 : bl;
+            int y = (c > r) ? pb + bl : (c == r ? 0 : kNeg16);
+            y = valid ? y : kNeg16;
+            ws.y[r & 1][c] = (int16_t)y;
+            __syncwarp();
+            const uint4 *yp = reinterpret_cast<const uint4 *>(ws.y[r & 1]);
+            unsigned a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const uint4 a = yp[v];
+                const unsigned aw[4] = {a.x, a.y, a.z, a.w};
+                unsigned wp[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c0 = 8 * v + 2 * e, c1 = c0 + 1;
+                    const int r0 = (c0 + 1 <= T) ? c0 + 1 : T, r1 = (c1 + 1 <= T) ? c1 + 1 : T;
+                    const int t0 = (int)ws.tile[r0][c], t1 = (int)ws.tile[r1][c];
+                    const int w0 = (c0 < c && c0 >= r && c0 + 1 <= T) ? t0 : kNeg16;
+                    const int w1 = (c1 < c && c1 >= r && c1 + 1 <= T) ? t1 : kNeg16;
+                    wp[e] = (unsigned)(w0 & 0xffff) | ((unsigned)w1 << 16);
+                }
+                a0 = __viaddmax_s16x2(aw[0], wp[0], a0);
+                a1 = __viaddmax_s16x2(aw[1], wp[1], a1);
+                a2 = __viaddmax_s16x2(aw[2], wp[2], a2);
+                a3 = __viaddmax_s16x2(aw[3], wp[3], a3);
+            }
+            const unsigned acc = __vmaxs2(__vmaxs2(a0, a1), __vmaxs2(a2, a3));
+            int d = max(y, hmax2(acc));
+            d = (c < r || !valid) ? 0 : d;
+            publish(r, d, below);
+            below = d;
+        }
+    } else {
+        int yold = old_terms(T - 1);
+#pragma unroll 1
+        for (int r = T - 1; r >= 0; --r) {
+            if (r == T / 2 && P.trace) tdeps[1] = (long long)gtimer();
+            const int si = (int)ws.rcode[r];
+            const int pb = (int)((((unsigned)(pair64 >> (8 * si))) >> sj) & 1u);
+            // D(i+1, j-1): lane c-1's previous row; lane 0 reads the left column
+            int bl = __shfl_up_sync(FULL, below, 1);
+            const int lft = (int)ws.left[r + 1];
+            bl = (c == 0) ? lft : bl;
+            // fresh terms: pair, the split k = i+1 (D(i,i) + D(i+1,j)), and a group completed by row r+1
+            int y = max(max(yold, pb + bl), below);
+            if constexpr (TV) {
+                const int gl = r / Q;   // < G for every r < T
+                const uint32_t f = ws.drf[r][gl];
+                const uint32_t cb = ws.cbc[gl][c];
+                const int v = rlookup<Q>(Rs, hrow_offset<Q>((int)(f & C::BMASK)), (int)(cb & C::BMASK));
+                const int cand = (int)(f >> 16) + (int)(cb >> 16) + v;
+                y = (r % Q == 0) ? max(y, cand) : y;
+            }
+            y = valid ? y : kNeg16;
+            // closure over the row: D_c = max(Y_c, max_{c'<c} Y_c' + W[c'][c])
+            ws.y[r & 1][c] = (int16_t)y;
+            __syncwarp();
+            // old terms of the next row overlap with this closure (the last one is unused)
+            yold = old_terms(max(r - 1, 0));
+            const uint4 *yp = reinterpret_cast<const uint4 *>(ws.y[r & 1]);
+            unsigned a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const uint4 a = yp[v];
+                a0 = __viaddmax_s16x2(a.x, Wp[4 * v + 0], a0);
+                a1 = __viaddmax_s16x2(a.y, Wp[4 * v + 1], a1);
+                a2 = __viaddmax_s16x2(a.z, Wp[4 * v + 2], a2);
+                a3 = __viaddmax_s16x2(a.w, Wp[4 * v + 3], a3);
+            }
+            const unsigned acc = __vmaxs2(__vmaxs2(a0, a1), __vmaxs2(a2, a3));
+            int d = max(y, hmax2(acc));
+            d = valid ? d : 0;
+            publish(r, d, below);
+            below = d;
         }
     }
     __syncwarp();
-    // ---- store both copies: row-major rows (coalesced over lanes = columns) ...
-    if (valid) {
-#pragma unroll 4
-        for (int r = 0; r < T; ++r) Drow[(size_t)(IT + r) * Np + j] = ws.tile[r][c];
-    }
-    // ... and column-major columns (lane = row)
+    if (P.trace) tdeps[2] = (long long)gtimer();
+    // ---- column-major copy (lane = row)
     if (lane < T) {
-#pragma unroll 4
+#pragma unroll 8
         for (int cc = 0; cc < T; ++cc) Dcol[(size_t)(JT + cc) * PC + IT + lane + kColOff] = ws.tile[lane][cc];
     }
     // answer D(0, n-1)
     if (I == 0 && J == NT - 1) {
-        int cn = (sd.n - 1) - JT;
+        const int cn = (sd.n - 1) - JT;
         if (sd.n >= 1 && lane == cn) P.results[sd.result_index] = (sd.n >= 2) ? (int)ws.tile[0][cn] : 0;
     }
+    if (P.trace) tdeps[3] = (long long)gtimer();
     __threadfence();
     __syncwarp();
     if (lane == 0) st_release(flags + I * NT + J, 1);
+    return tfar;
 }
 
 // ---------------------------------------------------------------- kernel
@@ -485,8 +725,24 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
         const int4 tk = P.tasks[idx];
         const SeqDesc sd = P.seqs[tk.x];
         const int I = task_I(tk.y), J = task_J(tk.y);
-        if (task_type(tk.y) == kTaskNear) run_near<Q, M>(P, sd, I, J, tk.z, ws, Rs, lane);
-        else run_far<Q, M>(P, sd, I, J, tk.z, tk.w, ws, Rs, lane);
+        long long t0 = 0, tdeps[4] = {0, 0, 0, 0};
+        if (P.trace && lane == 0) t0 = (long long)gtimer();
+        long long tmid;
+        if (task_type(tk.y) == kTaskNear) tmid = run_near<Q, M>(P, sd, I, J, tk.z, ws, Rs, lane, tdeps);
+        else tmid = run_far<Q, M>(P, sd, I, J, tk.z, tk.w, ws, Rs, lane, tdeps);
+        if (P.trace && lane == 0) {
+            long long *rec = P.trace + (size_t)idx * kTraceWords;
+            rec[0] = ((long long)(blockIdx.x * kWarpsPerCta + warp) << 32) | (unsigned)idx;
+            rec[1] = ((long long)task_type(tk.y) << 32) | (unsigned)tk.x;
+            rec[2] = ((long long)I << 32) | (unsigned)J;
+            rec[3] = t0;
+            rec[4] = tdeps[0];
+            rec[5] = tmid;
+            rec[6] = (long long)gtimer();
+            rec[7] = tdeps[1];
+            rec[8] = tdeps[2];
+            rec[9] = tdeps[3];
+        }
     }
 }
 

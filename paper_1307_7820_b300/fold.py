@@ -20,6 +20,7 @@ FOLD_OK, FOLD_EINVAL, FOLD_ENOMEM, FOLD_EAGAIN, FOLD_ETIMEOUT, FOLD_ECUDA, FOLD_
 FOLD_METHOD_TWO_VECTOR, FOLD_METHOD_PLAIN = 0, 1
 FOLD_OPT_METHOD, FOLD_OPT_GRID, FOLD_OPT_TIMEOUT_MS, FOLD_OPT_KCHUNK = 1, 2, 3, 4
 FOLD_OPT_Q, FOLD_OPT_TILE, FOLD_OPT_LAUNCHES, FOLD_OPT_TEST_DROP_TASK = 5, 6, 7, 8
+FOLD_OPT_TIMING, FOLD_OPT_KERNEL_NS, FOLD_OPT_TRACE = 9, 10, 11
 FOLD_PAIRS_DEFAULT = 0x5A48   # AU UA CG GC GU UG
 FOLD_PAIRS_PAPER = 0x1248     # AU UA CG GC
 FOLD_MAX_N = 65535
@@ -28,8 +29,16 @@ FOLD_MAX_N = 65535
 ABI_SYMBOLS = (
     "fold_init", "fold_destroy", "fold_strerror", "fold_set_option", "fold_get_option", "fold_rtable",
     "fold_score", "fold_workspace_bytes", "fold_score_dev", "fold_batch",
-    "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop",
+    "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop", "fold_trace_copy",
 )
+
+
+class TraceRec(ctypes.Structure):
+    """struct fold_trace_rec"""
+    _fields_ = [("worker", ctypes.c_int32), ("task", ctypes.c_int32), ("type", ctypes.c_int32),
+                ("I", ctypes.c_int32), ("J", ctypes.c_int32), ("seq", ctypes.c_int32),
+                ("t_start", ctypes.c_int64), ("t_deps", ctypes.c_int64), ("t_mid", ctypes.c_int64),
+                ("t_end", ctypes.c_int64), ("t_aux", ctypes.c_int64 * 3)]
 
 _lib = None
 
@@ -69,6 +78,8 @@ def lib():
     L.fold_serve_submit.argtypes = [vp, ctypes.c_char_p, i32, P(ctypes.c_uint64)]
     L.fold_serve_poll.argtypes = [vp, ctypes.c_uint64, P(i32), vp]
     L.fold_serve_stop.argtypes = [vp]
+    L.fold_trace_copy.argtypes = [vp, vp, i64]
+    L.fold_trace_copy.restype = i64
     for name in ("fold_set_option", "fold_get_option", "fold_rtable", "fold_score", "fold_score_dev", "fold_batch",
                  "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop"):
         getattr(L, name).restype = ctypes.c_int
@@ -150,6 +161,17 @@ def fold_batch(ctx: int, seqs, want_D: bool = False):
     _check(lib().fold_batch(ctx, k, arr, lens, out, dptr), "fold_batch")
     res = np.array(list(out), dtype=np.int32)
     return (res, Ds) if want_D else res
+
+
+def fold_trace_copy(ctx: int, cap: int = 1 << 24) -> np.ndarray:
+    """Trace of the last traced launch as a numpy structured array."""
+    buf = (TraceRec * cap)()
+    k = lib().fold_trace_copy(ctx, buf, cap)
+    if k < 0:
+        raise FoldError(-k, "fold_trace_copy")
+    dt = np.dtype([("worker", "i4"), ("task", "i4"), ("type", "i4"), ("I", "i4"), ("J", "i4"), ("seq", "i4"),
+                   ("t_start", "i8"), ("t_deps", "i8"), ("t_mid", "i8"), ("t_end", "i8"), ("t_aux", "i8", (3,))])
+    return np.frombuffer(bytes(buf)[: k * ctypes.sizeof(TraceRec)], dtype=dt).copy()
 
 
 def fold_serve_start(ctx: int, budget_bytes: int, max_inflight: int = 4096) -> None:

@@ -265,3 +265,16 @@ def test_two_vector_structured_and_gc():
         s = synth.variant(kind, 400, 4242)
         for q in (4, 7, 9):
             assert np.array_equal(oracle.nussinov(s), oracle.two_vector(s, q))
+
+
+def test_metrics_lookup_count_matches_algorithm1():
+    """The closed-form lookup count used by the roofline equals the number of
+    table lookups Algorithm 1 actually makes."""
+    from paper_1307_7820_b300 import metrics
+    rng = np.random.default_rng(2)
+    for n, q in [(0, 8), (1, 8), (17, 4), (100, 8), (257, 8), (300, 9), (129, 3)]:
+        s = _rand_seq(rng, n)
+        _, nl = oracle.two_vector(s, q, return_lookups=True)
+        assert metrics.lookups(n, q) == nl == lookup_count(n, q)
+        assert metrics.splits(n) == sum(j - i for i in range(n) for j in range(i + 1, n))
+        assert metrics.residual_splits(n, q) >= 0
