@@ -568,6 +568,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         }
     };
 
+    uint32_t last_cb = 0;      // feature of the column group completed most recently
     // publishes row r (value d of this lane's column): tile copy, row-major store, vertical and
     // horizontal difference vectors
     auto publish = [&](int r, int d, int below_prev) {
@@ -580,12 +581,8 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             const int gl = max(r - 1, 0) / Q;
             const uint32_t cb = ((uint32_t)d << 16) | (vhist & C::BMASK);
             ws.cbc[done ? gl : G][c] = cb;
+            last_cb = done ? cb : last_cb;
             if (done && valid) P.cf[sd.cf_off + (size_t)(I * G + gl) * Np + j] = cb;
-            const int dl = __shfl_up_sync(FULL, d, 1);
-            const unsigned hb = __ballot_sync(FULL, (d - dl) == 1);
-            const int a = __shfl_sync(FULL, d, (c < G) ? c * Q : 0);
-            if (c < G)
-                P.rf[sd.rf_off + (size_t)(IT + r) * NG + J * G + c] = ((uint32_t)a << 16) | ((hb >> (c * Q + 1)) & C::BMASK);
         } else {
             // row r joins the column pairs used by the rows above
             const int mm = max(r - 1, 0) >> 1;
@@ -651,9 +648,9 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             // fresh terms: pair, the split k = i+1 (D(i,i) + D(i+1,j)), and a group completed by row r+1
             int y = max(max(yold, pb + bl), below);
             if constexpr (TV) {
-                const int gl = r / Q;   // < G for every r < T
+                const int gl = r / Q;   // < G for every r < T; completed by row r+1 when r % Q == 0
                 const uint32_t f = ws.drf[r][gl];
-                const uint32_t cb = ws.cbc[gl][c];
+                const uint32_t cb = last_cb;
                 const int v = rlookup<Q>(Rs, hrow_offset<Q>((int)(f & C::BMASK)), (int)(cb & C::BMASK));
                 const int cand = (int)(f >> 16) + (int)(cb >> 16) + v;
                 y = (r % Q == 0) ? max(y, cand) : y;
@@ -683,6 +680,28 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     }
     __syncwarp();
     if (P.trace) tdeps[2] = (long long)gtimer();
+    if constexpr (TV) {
+        // horizontal difference vectors of the finished rows, packed with one ballot per row (bit c =
+        // D(i,JT+c) - D(i,JT+c-1)); the rows are independent, so their shuffle/ballot chains overlap
+        // all tile reads first (a ballot is a warp-synchronous point that loads are not moved across)
+        bool up[T];
+        int av[T];
+#pragma unroll
+        for (int r = 0; r < T; ++r) {
+            const int d = (int)ws.tile[r][c];
+            const int dl = (int)ws.tile[r][c > 0 ? c - 1 : 0];
+            up[r] = (d - dl) == 1;
+            av[r] = (int)ws.tile[r][(c < G) ? c * Q : 0];
+        }
+        unsigned hb[T];
+#pragma unroll
+        for (int r = 0; r < T; ++r) hb[r] = __ballot_sync(FULL, up[r]);
+        if (c < G) {
+#pragma unroll
+            for (int r = 0; r < T; ++r)
+                P.rf[sd.rf_off + (size_t)(IT + r) * NG + J * G + c] = ((uint32_t)av[r] << 16) | ((hb[r] >> (c * Q + 1)) & C::BMASK);
+        }
+    }
     // ---- column-major copy (lane = row)
     if (lane < T) {
 #pragma unroll 8
