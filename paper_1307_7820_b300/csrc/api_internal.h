@@ -73,4 +73,6 @@ int kc_auto(int NT);
 int status_from_cuda(cudaError_t e);
 cudaError_t launch_fold_instrumented(fold_ctx *ctx, FoldParams &p, cudaStream_t st);
 bool encode_seq(const char *seq, int n, uint8_t *out);
+int ensure_buf(DevBuf &b, size_t bytes);
+int ensure_host(HostBuf &b, size_t bytes);
 }  // namespace fold

@@ -78,4 +78,19 @@ void build_schedule(const std::vector<int> &NTs, int kc, std::vector<int4> &out)
     }
 }
 
+void build_schedule_steps(int NT, int kc, std::vector<int4> &out, std::vector<int> &step_begin) {
+    std::vector<int> nts(1, NT);
+    build_schedule(nts, kc, out);
+    // tasks are emitted step by step: NEAR tasks of diagonal t, then the chunks placed at t
+    step_begin.assign(NT + 1, (int)out.size());
+    int t = -1;
+    for (int k = 0; k < (int)out.size(); ++k) {
+        if (task_type(out[k].y) == kTaskNear) {
+            int d = task_J(out[k].y) - task_I(out[k].y);
+            while (t < d) step_begin[++t] = k;
+        }
+    }
+    step_begin[NT] = (int)out.size();
+}
+
 }  // namespace fold

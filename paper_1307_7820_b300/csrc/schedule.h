@@ -9,4 +9,9 @@ namespace fold {
 // number of middle tile columns merged by one FAR chunk.
 void build_schedule(const std::vector<int> &NTs, int kc, std::vector<int4> &out);
 
+// Same list for one sequence, with step_begin[t] = index of the first task of
+// step t (the NEAR tasks of tile diagonal t and the chunks placed after them);
+// step_begin[NT] = out.size().
+void build_schedule_steps(int NT, int kc, std::vector<int4> &out, std::vector<int> &step_begin);
+
 }  // namespace fold

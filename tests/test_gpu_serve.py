@@ -1,0 +1,93 @@
+"""Serving (continuous batching) on the GPU: requests that arrive while
+others are in flight are admitted as memory frees up, share persistent
+launches with them, and every result equals the one the same sequence gives
+alone (exactly: the work is integer).  All calls go through the C-ABI."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1307_7820_b300 import fold, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _drain(ctx, tickets, timeout=120.0, want_D=None):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t in out:
+                continue
+            D = want_D.get(t) if want_D else None
+            r = fold.fold_serve_poll(ctx, t, D)
+            if r is not None:
+                out[t] = r
+        assert time.time() - t0 < timeout, "serving did not finish"
+        time.sleep(0.001)
+    return out
+
+
+def test_serve_mix_equals_alone():
+    f = fold.Folder(q=8)
+    try:
+        kinds = ["uniform", "gc_rich", "structured"]
+        lens = [0, 1, 2, 31, 32, 33, 100, 500, 1200, 64, 2500, 7, 300, 900]
+        seqs = [synth.variant(kinds[k % 3], L, 900 + k) for k, L in enumerate(lens)]
+        alone = [f.score(s) for s in seqs]
+        fold.fold_serve_start(f.ctx, 8 << 30, 64)
+        tickets = []
+        # staggered arrivals: some while others are already on the GPU
+        for k, s in enumerate(seqs):
+            tickets.append(fold.fold_serve_submit(f.ctx, s))
+            if k % 4 == 3:
+                time.sleep(0.002)
+        res = _drain(f.ctx, tickets)
+        got = [res[t] for t in tickets]
+        assert got == alone
+        assert got == [oracle.score(s) if len(s) else 0 for s in seqs]
+    finally:
+        fold.fold_serve_stop(f.ctx)
+        f.close()
+
+
+def test_serve_budget_admission_and_tables():
+    f = fold.Folder(q=8)
+    try:
+        one = f.workspace_bytes(800)
+        # room for about three 800-base requests at a time
+        fold.fold_serve_start(f.ctx, int(3.5 * one), 16)
+        seqs = [synth.uniform(800, 40 + k) for k in range(10)]
+        tickets = [fold.fold_serve_submit(f.ctx, s) for s in seqs]
+        Ds = {t: np.zeros((800, 800), dtype=np.int16) for t in tickets[:3]}
+        res = _drain(f.ctx, tickets, want_D=Ds)
+        for t, s in zip(tickets, seqs):
+            assert res[t] == oracle.score(s)
+        for t, s in zip(tickets[:3], seqs[:3]):
+            assert np.array_equal(Ds[t].astype(np.int32), oracle.nussinov(s))
+        # a request that can never fit the budget is refused, not queued forever
+        with pytest.raises(fold.FoldError) as ei:
+            fold.fold_serve_submit(f.ctx, synth.uniform(4000, 1))
+        assert ei.value.code == fold.FOLD_EAGAIN
+    finally:
+        fold.fold_serve_stop(f.ctx)
+        f.close()
+
+
+def test_serve_poll_unknown_ticket_and_restart():
+    f = fold.Folder(q=8)
+    try:
+        fold.fold_serve_start(f.ctx, 1 << 28, 4)
+        with pytest.raises(fold.FoldError) as ei:
+            fold.fold_serve_poll(f.ctx, 123456)
+        assert ei.value.code == fold.FOLD_EINVAL
+        t = fold.fold_serve_submit(f.ctx, "GGGAAAUCC")
+        assert _drain(f.ctx, [t])[t] == 3
+        fold.fold_serve_stop(f.ctx)
+        fold.fold_serve_start(f.ctx, 1 << 28, 4)
+        t = fold.fold_serve_submit(f.ctx, "ACUGACUG")
+        assert _drain(f.ctx, [t])[t] == 3
+    finally:
+        fold.fold_serve_stop(f.ctx)
+        f.close()
