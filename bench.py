@@ -48,6 +48,9 @@ def parse_args():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--trace", default="", help="write a per-task trace of one fold to this .npy file")
+    ap.add_argument("--serve-rates", default="200,1000",
+                    help="Poisson arrival rates (req/s) for the serving run; the workload lists 50-2000")
+    ap.add_argument("--serve-seconds", type=float, default=1.5, help="arrival window per rate")
     return ap.parse_args()
 
 
@@ -156,6 +159,82 @@ def run_reference(a):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------------------------ serving
+def serve_bench(f, rates, seconds, dev, stream, torch, fold, metrics, synth):
+    """Continuous batching under Poisson arrivals vs folding the same requests one at a time."""
+    import threading
+    out = []
+    budget = 60 << 30
+    for ri, rate in enumerate(rates):
+        count = max(8, int(rate * seconds))
+        reqs = synth.serve_requests(rate, count, 50, 8000, synth.SEED_BASE + 4 + ri)
+        fold.fold_serve_start(f.ctx, budget, 4096)
+        submit_t = {}
+        done_t = {}
+        tickets = [None] * count
+        t0 = time.perf_counter()
+
+        def submitter():
+            for k, (at, s, _) in enumerate(reqs):
+                while time.perf_counter() - t0 < at:
+                    time.sleep(0.0002)
+                submit_t[k] = time.perf_counter()
+                while True:
+                    try:
+                        tickets[k] = fold.fold_serve_submit(f.ctx, s)
+                        break
+                    except fold.FoldError as e:
+                        if e.code != fold.FOLD_EAGAIN:
+                            raise
+                        time.sleep(0.001)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        pending = set(range(count))
+        results = {}
+        while pending:
+            for k in list(pending):
+                if tickets[k] is None:
+                    continue
+                r = fold.fold_serve_poll(f.ctx, tickets[k])
+                if r is not None:
+                    done_t[k] = time.perf_counter()
+                    results[k] = r
+                    pending.discard(k)
+            time.sleep(0.0002)
+        th.join()
+        wall = max(done_t.values()) - t0
+        fold.fold_serve_stop(f.ctx)
+        lat = np.array([1e3 * (done_t[k] - submit_t[k]) for k in range(count)])
+        # one at a time: device time of every 8th request folded alone, scaled to all
+        alone_s = 0.0
+        sample = list(range(0, count, 8))
+        for k in sample:
+            s = reqs[k][1]
+            codes = torch.from_numpy(fold.encode_codes(s)).to(dev)
+            ws = torch.empty(max(256, f.workspace_bytes(len(s))), dtype=torch.uint8, device=dev)
+            o = torch.zeros(1, dtype=torch.int32, device=dev)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f.score_dev(codes, ws, o, None, stream=stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            alone_s += e0.elapsed_time(e1) / 1e3
+            assert int(o.item()) == results[k]
+        alone_s *= count / len(sample)
+        cells = sum(metrics.cells(len(r[1])) for r in reqs)
+        out.append({"rate_req_s": rate, "requests": count, "p50_ms": float(np.percentile(lat, 50)),
+                    "p99_ms": float(np.percentile(lat, 99)), "throughput_req_s": count / wall,
+                    "throughput_cells_s": cells / wall,
+                    "one_at_a_time_req_s": count / alone_s,
+                    "one_at_a_time_note": "device time of every 8th request folded alone, scaled to all",
+                    "lengths": "log-uniform [50, 8000]; 80% uniform, 10% GC-rich, 10% structured",
+                    "budget_bytes": budget})
+    return out
 
 
 # ------------------------------------------------------------------ GPU side
@@ -306,6 +385,12 @@ def main():
                  "one_at_a_time_sample": "device time of every 16th sequence, scaled to 4096",
                  "total_cells": int(sum(metrics.cells(len(s)) for s in seqs)), "checksum": int(res.sum())}
 
+    # ---- serving: Poisson arrivals, lengths log-uniform in [50, 8000], 60 GB D budget
+    serve = None
+    if not a.no_serve:
+        serve = serve_bench(tv, [float(x) for x in a.serve_rates.split(",") if x], a.serve_seconds, dev, stream,
+                            torch, fold, metrics, synth)
+
     # ---- CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
     cpu = None
     if not a.no_cpu and rank == 0 and world == 1:
@@ -337,7 +422,7 @@ def main():
         "plain": {"ms_per_step": pl_ms, "cells_per_s": cells / (pl_ms * 1e-3),
                   "two_vector_speedup": pl_ms / statistics.mean(r_tv["step_ms"]),
                   "kernel_ms": statistics.mean(r_pl["kern_ms"])},
-        "batch": batch, "serve": None,
+        "batch": batch, "serve": serve,
         "max_pairs": r_tv["max_pairs"],
     }
     if rank == 0:
