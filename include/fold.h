@@ -45,6 +45,7 @@ extern "C" {
 #define FOLD_MAX_N 65535
 #define FOLD_PAIRS_DEFAULT ((uint16_t)0x5A48)
 #define FOLD_PAIRS_PAPER ((uint16_t)0x1248)
+#define FOLD_STATIC_MAX_N 1024
 
 typedef struct fold_ctx fold_ctx;
 
@@ -152,6 +153,31 @@ int fold_score_dev(fold_ctx *ctx, const uint8_t *d_codes, int32_t n, void *d_ws,
  * D_out[k] (else lens[k]*lens[k] int16).  Synchronous. */
 int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int32_t *lens,
                int32_t *max_pairs_out, int16_t *const *D_out);
+
+/* Allocation-free fold.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc when they fold -- code
+ * running inside a framework whose own allocator must own all device memory,
+ * services that allocate everything at start-up and must not allocate or
+ * implicitly synchronise the device on the request path, plugins and
+ * callbacks where allocation is not permitted.  It needs no context and no
+ * workspace: its scratch is one fixed 8 MiB device array inside this library,
+ * which every GPU that loads the library holds until the process exits.
+ *   d_codes     n device bytes with codes 0..3;
+ *   n           0 <= n <= FOLD_STATIC_MAX_N (1024), else FOLD_EINVAL;
+ *   pair_mask   as for fold_init;
+ *   d_max_pairs one device int32: D(0,n-1), or -FOLD_ETIMEOUT;
+ *   d_D_out     nullable device buffer of n*n int16 for the full table;
+ *   stream      cudaStream_t (NULL = the CUDA default stream); the call is
+ *               enqueued there and returns without waiting.
+ * Two-vector method with q = 8 on the current device.  It allocates no device
+ * memory (no cudaMalloc, cudaFree or allocating library call).  All calls
+ * share the one scratch array, so calls that overlap on the GPU (different
+ * streams or threads) race and corrupt each other: serialise them.  The first
+ * call on a device does that device's set-up (finds the array's device
+ * address, builds the R table, synchronises the stream); make it before any
+ * stream capture. */
+int fold_score_static(const uint8_t *d_codes, int32_t n, uint16_t pair_mask, int32_t *d_max_pairs,
+                      int16_t *d_D_out, void *stream);
 
 /* Serving (continuous batching).  fold_serve_start starts a host scheduler
  * thread that admits submitted requests while the device memory their two

@@ -24,12 +24,14 @@ FOLD_OPT_TIMING, FOLD_OPT_KERNEL_NS, FOLD_OPT_TRACE = 9, 10, 11
 FOLD_PAIRS_DEFAULT = 0x5A48   # AU UA CG GC GU UG
 FOLD_PAIRS_PAPER = 0x1248     # AU UA CG GC
 FOLD_MAX_N = 65535
+FOLD_STATIC_MAX_N = 1024
 
 #: every symbol include/fold.h declares
 ABI_SYMBOLS = (
     "fold_init", "fold_destroy", "fold_strerror", "fold_set_option", "fold_get_option", "fold_rtable",
     "fold_score", "fold_workspace_bytes", "fold_score_dev", "fold_batch",
     "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop", "fold_trace_copy",
+    "fold_score_static",
 )
 
 
@@ -79,6 +81,8 @@ def lib():
     L.fold_serve_poll.argtypes = [vp, ctypes.c_uint64, P(i32), vp]
     L.fold_serve_stop.argtypes = [vp]
     L.fold_trace_copy.argtypes = [vp, vp, i64]
+    L.fold_score_static.argtypes = [vp, i32, u16, vp, vp, vp]
+    L.fold_score_static.restype = ctypes.c_int
     L.fold_trace_copy.restype = i64
     for name in ("fold_set_option", "fold_get_option", "fold_rtable", "fold_score", "fold_score_dev", "fold_batch",
                  "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop"):
@@ -172,6 +176,12 @@ def fold_trace_copy(ctx: int, cap: int = 1 << 24) -> np.ndarray:
     dt = np.dtype([("worker", "i4"), ("task", "i4"), ("type", "i4"), ("I", "i4"), ("J", "i4"), ("seq", "i4"),
                    ("t_start", "i8"), ("t_deps", "i8"), ("t_mid", "i8"), ("t_end", "i8"), ("t_aux", "i8", (3,))])
     return np.frombuffer(bytes(buf)[: k * ctypes.sizeof(TraceRec)], dtype=dt).copy()
+
+
+def fold_score_static(d_codes: int | None, n: int, pair_mask: int, d_max_pairs: int,
+                      d_D_out: int | None = None, stream: int | None = None) -> None:
+    """Allocation-free fold of up to FOLD_STATIC_MAX_N bases (device pointers as ints)."""
+    _check(lib().fold_score_static(d_codes, n, pair_mask, d_max_pairs, d_D_out, stream), "fold_score_static")
 
 
 def fold_serve_start(ctx: int, budget_bytes: int, max_inflight: int = 4096) -> None:
