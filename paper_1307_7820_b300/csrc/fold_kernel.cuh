@@ -58,14 +58,17 @@ static __device__ __noinline__ bool wait_geq_impl(const int *p, int target, int 
     int ok = 1;
     if (lane == 0) {
         if (ld_acquire(p) < target) {
-            unsigned long long t0 = gtimer();
-            unsigned ns = 32;
+            // poll without sleeping for the first 2 us (dependencies usually resolve within a few
+            // L2 round trips), then back off to at most 256 ns between polls
+            const unsigned long long t0 = gtimer();
+            unsigned ns = 0;
             for (;;) {
-                __nanosleep(ns);
-                if (ns < 256) ns <<= 1;
+                if (ns) __nanosleep(ns);
                 if (ld_acquire(p) >= target) break;
                 if (*(volatile int *)error != 0) { ok = 0; break; }
-                if ((long long)(gtimer() - t0) > timeout_ns) {
+                const long long el = (long long)(gtimer() - t0);
+                if (el > 2000) ns = ns ? (ns < 256 ? 2 * ns : 256) : 32;
+                if (el > timeout_ns) {
                     atomicCAS(error, 0, kErrTimeout);
                     ok = 0;
                     break;
@@ -189,6 +192,54 @@ __device__ __forceinline__ void far_block_tv(const FoldParams &P, const SeqDesc 
     __syncwarp();
 }
 
+// A chunk of middle blocks [Ka, Kb]: the features of block K+1 are loaded while
+// block K is evaluated, so each block's L2 latency overlaps the previous block.
+template <int Q>
+__device__ __forceinline__ void far_chunk_tv(const FoldParams &P, const SeqDesc &sd, int I, int J, int Ka, int Kb,
+                                             int *m, WarpScratch<Q, kTwoVector> &ws, const uint8_t *Rs, int lane) {
+    using C = Cfg<Q, kTwoVector>;
+    constexpr int T = C::T, G = C::G;
+    const int Np = sd.Np, NG = Np / Q;
+    const uint32_t *RF = P.rf + sd.rf_off;
+    const uint32_t *CF = P.cf + sd.cf_off;
+    const bool valid = lane < T;
+    uint32_t cfn[G], rfn[G];
+#pragma unroll
+    for (int gl = 0; gl < G; ++gl) {
+        const int g = Ka * G + gl;
+        cfn[gl] = valid ? __ldcg(CF + (size_t)g * Np + J * T + lane) : 0u;
+        rfn[gl] = valid ? __ldcg(RF + (size_t)(I * T + lane) * NG + g) : 0u;
+    }
+    for (int K = Ka; K <= Kb; ++K) {
+        int B[G], Cv[G];
+#pragma unroll
+        for (int gl = 0; gl < G; ++gl) {
+            B[gl] = (int)(cfn[gl] >> 16);
+            Cv[gl] = (int)(cfn[gl] & C::BMASK);
+            ws.rf[gl][lane] = make_int2((int)(rfn[gl] >> 16), hrow_offset<Q>((int)(rfn[gl] & C::BMASK)));
+        }
+        if (K < Kb) {   // prefetch the next block
+#pragma unroll
+            for (int gl = 0; gl < G; ++gl) {
+                const int g = (K + 1) * G + gl;
+                cfn[gl] = valid ? __ldcg(CF + (size_t)g * Np + J * T + lane) : 0u;
+                rfn[gl] = valid ? __ldcg(RF + (size_t)(I * T + lane) * NG + g) : 0u;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int gl = 0; gl < G; ++gl) {
+#pragma unroll
+            for (int r = 0; r < T; ++r) {
+                const int2 f = ws.rf[gl][r];
+                const int v = rlookup<Q>(Rs, f.y, Cv[gl]);
+                m[r] = max(m[r], f.x + B[gl] + v);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Plain: m[r] holds two packed int16 partial maxima; splits k in [KT+1, KT+T].
 static __device__ __forceinline__ void far_block_plain(const FoldParams &P, const SeqDesc &sd, int I, int J, int K,
                                                 unsigned *m, WarpScratch<8, kPlain> &ws, int lane) {
@@ -264,7 +315,7 @@ __device__ __forceinline__ long long run_far(const FoldParams &P, const SeqDesc 
     if constexpr (M == kTwoVector) {
 #pragma unroll
         for (int r = 0; r < T; ++r) m[r] = 0;
-        for (int K = Ka; K <= Kb; ++K) far_block_tv<Q>(P, sd, I, J, K, m, ws, Rs, lane);
+        far_chunk_tv<Q>(P, sd, I, J, Ka, Kb, m, ws, Rs, lane);
     } else {
         unsigned mp[T];
 #pragma unroll
@@ -321,6 +372,14 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         for (int v = 0; v < 16; ++v) lcol[k][v] = 0;
     }
     if (valid) ws.rcode[c] = codes[IT + c];
+    // pair bits of this lane's column against the tile's 32 rows: bit r = b(S_{IT+r}, S_j)
+    const int sj = valid ? (int)codes[j] : kPadCode;
+    unsigned pbits = 0;
+#pragma unroll
+    for (int r = 0; r < T; ++r) {
+        const int si = (int)codes[IT + r];
+        pbits |= (unsigned)((P.pair64 >> (8 * si + sj)) & 1ull) << r;
+    }
     if (t >= 1) {
         if (!warp_wait_geq(flags + I * NT + I, 1, P, lane)) return 0;
         if (!warp_wait_geq(flags + J * NT + J, 1, P, lane)) return 0;
@@ -394,6 +453,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         if (!warp_wait_geq(flags + (I + 1) * NT + J, 1, P, lane)) return 0;
     }
     if (P.trace) tdeps[0] = (long long)gtimer();
+    // every load that depends on the neighbours goes out at once
     int colT = 0;              // D((I+1)T, j): row 0 of tile (I+1, J)
     int leftv = 0;             // D(IT+1+c, JT-1): left column for lane 0's pair term
     if (t >= 1 && valid) {
@@ -401,36 +461,27 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         const int row = IT + 1 + c;
         if (row <= JT - 1 && row < Np) leftv = ldcg16(Dcol + (size_t)(JT - 1) * PC + row + kColOff);
     }
+    constexpr int E = (T * G + 31) / 32;
+    uint32_t fa[E];            // row features of tile (I, J-1) (two-vector, late block K = J-1)
+    uint4 ra[4];               // row strip of tile (I, J-1), row IT+lane (plain)
     if constexpr (TV) {
-        if (lateA) {
-            constexpr int E = (T * G + 31) / 32;
-            uint32_t fa[E];
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int idx = e * 32 + lane;
-                fa[e] = idx < T * G ? __ldcg(RF + (size_t)(IT + idx / G) * NG + (J - 1) * G + idx % G) : 0u;
-            }
-            if (lateB && valid) {
+        for (int e = 0; e < E; ++e) {
+            const int idx = e * 32 + lane;
+            fa[e] = (lateA && idx < T * G) ? __ldcg(RF + (size_t)(IT + idx / G) * NG + (J - 1) * G + idx % G) : 0u;
+        }
+        if (lateB && valid) {
 #pragma unroll
-                for (int gl = 0; gl < G; ++gl) {
-                    const uint32_t cf = __ldcg(CF + (size_t)((I + 1) * G + gl) * Np + j);
-                    lB[1][gl] = (int)(cf >> 16);
-                    lC[1][gl] = (int)(cf & C::BMASK);
-                }
-            }
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int idx = e * 32 + lane;
-                if (idx < T * G) ws.lrf[0][idx / G][idx % G] = fa[e];
+            for (int gl = 0; gl < G; ++gl) {
+                const uint32_t cf = __ldcg(CF + (size_t)((I + 1) * G + gl) * Np + j);
+                lB[1][gl] = (int)(cf >> 16);
+                lC[1][gl] = (int)(cf & C::BMASK);
             }
         }
     } else {
-        if (lateA) {   // row strip of tile (I, J-1), row IT+lane
-            const uint4 *src = reinterpret_cast<const uint4 *>(Drow + (size_t)(IT + lane) * Np + (J - 1) * T);
-            uint4 *dst = reinterpret_cast<uint4 *>(&ws.lrow[0][lane][0]);
+        const uint4 *src = reinterpret_cast<const uint4 *>(Drow + (size_t)(IT + lane) * Np + (J - 1) * T);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) dst[v] = __ldcg(src + v);
-        }
+        for (int v = 0; v < 4; ++v) ra[v] = lateA ? __ldcg(src + v) : make_uint4(0u, 0u, 0u, 0u);
         if (lateB) {   // column j of tile (I+1, J): rows (I+1)T+1 .. (I+2)T
             const uint4 *cs = reinterpret_cast<const uint4 *>(Dcol + (size_t)j * PC + (I + 1) * T + 1 + kColOff);
 #pragma unroll
@@ -440,48 +491,76 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             }
         }
     }
-    // an absent late block gets neutral data (zero features / zero rows), so the row loop can
-    // evaluate both blocks unconditionally
-    if constexpr (TV) {
-        if (!lateA) {
-            constexpr int E = (T * G + 31) / 32;
+    // partial max of the FAR chunks (middle blocks I+2 .. J-2)
+    int acc[T];
+    int *slot = P.pring + sd.p_off + ((size_t)(t % kRing) * NT + I) * (T * T);
+    if (nfar > 0) {
+        if (!warp_wait_geq(P.cnt + sd.cnt_off + I * NT + J, nfar, P, lane)) return 0;
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int idx = e * 32 + lane;
-                if (idx < T * G) ws.lrf[0][idx / G][idx % G] = 0u;
+        for (int r = 0; r < T; ++r) acc[r] = valid ? __ldcg(slot + r * T + c) : 0;
+    } else {
+#pragma unroll
+        for (int r = 0; r < T; ++r) acc[r] = 0;
+    }
+    if constexpr (TV) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int idx = e * 32 + lane;
+            if (idx < T * G) ws.lrf[0][idx / G][idx % G] = fa[e];
+        }
+    } else {
+        uint4 *dst = reinterpret_cast<uint4 *>(&ws.lrow[0][lane][0]);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) dst[v] = ra[v];
+    }
+    __syncwarp();
+    // the two late middle blocks for every row at once (independent lookups, high ILP)
+    if constexpr (TV) {
+#pragma unroll
+        for (int kb = 0; kb < 2; ++kb) {
+            if (kb == 0 ? lateA : lateB) {
+#pragma unroll
+                for (int gl = 0; gl < G; ++gl) {
+#pragma unroll
+                    for (int r = 0; r < T; ++r) {
+                        const uint32_t f = ws.lrf[kb][r][gl];
+                        const int v = rlookup<Q>(Rs, hrow_offset<Q>((int)(f & C::BMASK)), lC[kb][gl]);
+                        acc[r] = max(acc[r], (int)(f >> 16) + lB[kb][gl] + v);
+                    }
+                }
             }
         }
     } else {
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            if (k == 0 ? !lateA : !lateB) {
-                uint4 *dst = reinterpret_cast<uint4 *>(&ws.lrow[k][lane][0]);
+        for (int kb = 0; kb < 2; ++kb) {
+            if (kb == 0 ? lateA : lateB) {
 #pragma unroll
-                for (int v = 0; v < 4; ++v) dst[v] = make_uint4(0u, 0u, 0u, 0u);
+                for (int r = 0; r < T; ++r) {
+                    const uint4 *rw = reinterpret_cast<const uint4 *>(&ws.lrow[kb][r][0]);
+                    unsigned a0 = 0, a1 = 0;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const uint4 a = rw[v];
+                        a0 = __viaddmax_s16x2(a.x, lcol[kb][4 * v + 0], a0);
+                        a1 = __viaddmax_s16x2(a.y, lcol[kb][4 * v + 1], a1);
+                        a0 = __viaddmax_s16x2(a.z, lcol[kb][4 * v + 2], a0);
+                        a1 = __viaddmax_s16x2(a.w, lcol[kb][4 * v + 3], a1);
+                    }
+                    acc[r] = max(acc[r], hmax2(__vmaxs2(a0, a1)));
+                }
             }
         }
     }
-    // partial max of the FAR chunks (middle blocks I+2 .. J-2), staged per row in shared memory
-    if (nfar > 0) {
-        if (!warp_wait_geq(P.cnt + sd.cnt_off + I * NT + J, nfar, P, lane)) return 0;
-        int *slot = P.pring + sd.p_off + ((size_t)(t % kRing) * NT + I) * (T * T);
-        if (valid) {
-            int pv[T];
+    if (valid) {
 #pragma unroll
-            for (int r = 0; r < T; ++r) pv[r] = __ldcg(slot + r * T + c);
+        for (int r = 0; r < T; ++r) ws.pm[r][c] = (int16_t)acc[r];
+        if (nfar > 0) {
 #pragma unroll
-            for (int r = 0; r < T; ++r) {
-                ws.pm[r][c] = (int16_t)pv[r];
-                __stcg(slot + r * T + c, 0);   // ring slot reused by tile (I, J+kRing)
-            }
+            for (int r = 0; r < T; ++r) __stcg(slot + r * T + c, 0);   // ring slot reused by tile (I, J+kRing)
         }
-    } else if (valid) {
-#pragma unroll
-        for (int r = 0; r < T; ++r) ws.pm[r][c] = 0;
     }
     const long long tfar = P.trace ? (long long)gtimer() : 0;
 
-    const int sj = valid ? (int)codes[j] : kPadCode;
     if (valid) {
         ws.left[c + 1] = (int16_t)leftv;
         ws.tile[T][c] = (int16_t)colT;
@@ -496,33 +575,29 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     }
     __syncwarp();
 
-    const unsigned long long pair64 = P.pair64;
     unsigned vhist = 0;        // vertical differences, newest in bit 0
+    // residual window (two-vector): win[e] = D(IT+r+1+e, j) while row r is being computed
+    constexpr int NW = Q > 2 ? Q - 2 : 1;
+    int win[NW];
+#pragma unroll
+    for (int e = 0; e < NW; ++e) win[e] = 0;
+    win[0] = colT;
 
     // terms of row rr that do not depend on row rr+1 (computed while row rr+1 closes); branch-free:
     // every candidate is evaluated with in-range indices and the invalid ones are masked
     auto old_terms = [&](int rr) -> int {
         if constexpr (TV) {
-            constexpr int NC = 1 + 2 * G + (Q > 2 ? Q - 2 : 0) + G;
+            constexpr int NC = 1 + (Q > 2 ? Q - 2 : 0) + G;
             int cand[NC];
             int k = 0;
             cand[k++] = (int)ws.pm[rr][c];
-#pragma unroll
-            for (int kb = 0; kb < 2; ++kb) {
-#pragma unroll
-                for (int gl = 0; gl < G; ++gl) {
-                    const uint32_t f = ws.lrf[kb][rr][gl];
-                    const int v = rlookup<Q>(Rs, hrow_offset<Q>((int)(f & C::BMASK)), lC[kb][gl]);
-                    cand[k++] = (int)(f >> 16) + lB[kb][gl] + v;
-                }
-            }
             const int ce = (rr + Q - 1) / Q * Q;
             // residual splits k in [i+2, IT+ce] (k = i+1 is the fresh D(i+1,j) term)
 #pragma unroll
             for (int e = 0; e < Q - 2; ++e) {
                 const int kk = rr + 2 + e;
                 const int ix = min(kk, T);
-                const int v = (int)ws.diag[rr][ix - 1] + (int)ws.tile[ix][c];
+                const int v = (int)ws.diag[rr][ix - 1] + win[e];
                 cand[k++] = (kk <= ce) ? v : kNeg16;
             }
             // full groups of tile column I completed before row rr+1 (g*q > rr)
@@ -535,21 +610,6 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             }
             return tree_max<NC>(cand);
         } else {
-            unsigned acc[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) acc[q] = 0;
-#pragma unroll
-            for (int kb = 0; kb < 2; ++kb) {
-                const uint4 *rw = reinterpret_cast<const uint4 *>(&ws.lrow[kb][rr][0]);
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const uint4 a = rw[v];
-                    acc[4 * kb + 0] = __viaddmax_s16x2(a.x, lcol[kb][4 * v + 0], acc[4 * kb + 0]);
-                    acc[4 * kb + 1] = __viaddmax_s16x2(a.y, lcol[kb][4 * v + 1], acc[4 * kb + 1]);
-                    acc[4 * kb + 2] = __viaddmax_s16x2(a.z, lcol[kb][4 * v + 2], acc[4 * kb + 2]);
-                    acc[4 * kb + 3] = __viaddmax_s16x2(a.w, lcol[kb][4 * v + 3], acc[4 * kb + 3]);
-                }
-            }
             // every split with D(k,j) in this tile column: rows not yet done hold the sentinel
             unsigned acc2[4] = {0u, 0u, 0u, 0u};
             const uint4 *dw = reinterpret_cast<const uint4 *>(&ws.diag[rr][0]);
@@ -561,10 +621,8 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
                 acc2[2] = __viaddmax_s16x2(a.z, ws.colpk[4 * v + 2][c], acc2[2]);
                 acc2[3] = __viaddmax_s16x2(a.w, ws.colpk[4 * v + 3][c], acc2[3]);
             }
-            const unsigned m4 = __vmaxs2(__vmaxs2(__vmaxs2(acc[0], acc[1]), __vmaxs2(acc[2], acc[3])),
-                                         __vmaxs2(__vmaxs2(acc[4], acc[5]), __vmaxs2(acc[6], acc[7])));
             const unsigned m2 = __vmaxs2(__vmaxs2(acc2[0], acc2[1]), __vmaxs2(acc2[2], acc2[3]));
-            return max((int)ws.pm[rr][c], hmax2(__vmaxs2(m4, m2)));
+            return max((int)ws.pm[rr][c], hmax2(m2));
         }
     };
 
@@ -599,8 +657,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll 1
         for (int r = T - 1; r >= 0; --r) {
             if (r == T / 2 && P.trace) tdeps[1] = (long long)gtimer();
-            const int si = (int)ws.rcode[r];
-            const int pb = (int)((((unsigned)(pair64 >> (8 * si))) >> sj) & 1u);
+            const int pb = (int)((pbits >> r) & 1u);
             int bl = __shfl_up_sync(FULL, below, 1);
             bl = (c == 0) ? 0 : bl;
             int y = (c > r) ? pb + bl : (c == r ? 0 : kNeg16);
@@ -639,8 +696,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll 1
         for (int r = T - 1; r >= 0; --r) {
             if (r == T / 2 && P.trace) tdeps[1] = (long long)gtimer();
-            const int si = (int)ws.rcode[r];
-            const int pb = (int)((((unsigned)(pair64 >> (8 * si))) >> sj) & 1u);
+            const int pb = (int)((pbits >> r) & 1u);
             // D(i+1, j-1): lane c-1's previous row; lane 0 reads the left column
             int bl = __shfl_up_sync(FULL, below, 1);
             const int lft = (int)ws.left[r + 1];
@@ -676,6 +732,11 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             d = valid ? d : 0;
             publish(r, d, below);
             below = d;
+            if constexpr (TV) {
+#pragma unroll
+                for (int e = NW - 1; e > 0; --e) win[e] = win[e - 1];
+                win[0] = d;
+            }
         }
     }
     __syncwarp();
