@@ -92,7 +92,7 @@ typedef struct fold_trace_rec {
     int64_t t_mid;      /* tile: ns when the partial max over middle blocks was complete;
                            chunk: ns when its lookups were done */
     int64_t t_end;      /* ns when its results were published */
-    int64_t t_aux[3];   /* tile only: half of the rows done, all rows done, stores issued */
+    int64_t t_aux[3];   /* tile only: chunk partial maxima ready (0 if none), all rows done, stores issued */
 } fold_trace_rec;
 
 /* Creates a context on `device`.  q in [2,10] is the vector length of
@@ -116,6 +116,16 @@ int fold_get_option(fold_ctx *ctx, int option, int64_t *value);
 /* Copies up to `cap` trace records of the last traced launch (FOLD_OPT_TRACE)
  * into out and returns how many were written (or a negative status). */
 int64_t fold_trace_copy(fold_ctx *ctx, fold_trace_rec *out, int64_t cap);
+
+/* Host-only self-check of the task list the persistent kernel would run for
+ * a single sequence of length n (no GPU needed): every middle block of every
+ * tile is merged exactly once, each tile's chunk count is right, and every
+ * task waits only on tasks placed before it, which is what makes the ordered
+ * list deadlock-free (Section 4 wavefront, replaced by dependency flags).
+ * kchunk = 0 picks the automatic chunk size.  Returns 0 if valid, a positive
+ * failure code otherwise, or -FOLD_EINVAL for bad arguments (n above 65535,
+ * or a tile count above 2048). */
+int fold_schedule_check(int32_t n, int q, int method, int32_t kchunk);
 
 /* Copies the R table to host memory: out[(h << (q-1)) | c] = R(h,c) for the
  * (q-1)-bit horizontal vector h and vertical vector c (bit p-1 holds

@@ -190,7 +190,7 @@ int single_schedule(fold_ctx *ctx, int n, const Plan &pl, const int4 **tasks, in
     auto it = ctx->sched_cache.find(key);
     if (it == ctx->sched_cache.end()) {
         std::vector<int4> tv;
-        build_schedule(pl.NTs, kc, tv);
+        build_schedule(pl.NTs, kc, strip_of(ctx->q, ctx->method), tv);
         if (ctx->test_drop_task) {
             // host-side fault injection: drop the NEAR task of tile (0,1)
             for (size_t k = 0; k < tv.size(); ++k)
@@ -424,6 +424,21 @@ int64_t fold_trace_copy(fold_ctx *ctx, fold_trace_rec *out, int64_t cap) {
     return count;
 }
 
+int fold_schedule_check(int32_t n, int q, int method, int32_t kchunk) {
+    if (n < 0 || n > FOLD_MAX_N || q < 2 || q > 10 || (method != FOLD_METHOD_TWO_VECTOR && method != FOLD_METHOD_PLAIN) ||
+        kchunk < 0)
+        return -FOLD_EINVAL;
+    if (n == 0) return 0;
+    const int T = tile_of(q, method);
+    const int NT = (n + T - 1) / T;
+    if (NT > 2048) return -FOLD_EINVAL;   // the check keeps NT^3 counters on the host
+    const int kc = kchunk > 0 ? kchunk : kc_auto(NT);
+    std::vector<int4> tv;
+    std::vector<int> nts(1, NT);
+    build_schedule(nts, kc, strip_of(q, method), tv);
+    return check_schedule(NT, kc, strip_of(q, method), tv);
+}
+
 int fold_rtable(fold_ctx *ctx, uint8_t *out, int64_t cap) {
     if (!ctx || !out) return FOLD_EINVAL;
     int64_t nent = (int64_t)1 << (2 * (ctx->q - 1));
@@ -492,7 +507,7 @@ int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int3
     for (int v : pl.NTs) maxNT = std::max(maxNT, v);
     int kc = ctx->kc_override > 0 ? ctx->kc_override : kc_auto(maxNT);
     std::vector<int4> tv;
-    build_schedule(pl.NTs, kc, tv);
+    build_schedule(pl.NTs, kc, strip_of(ctx->q, ctx->method), tv);
     // host staging: codes (padded) | SeqDesc | tasks | results
     size_t codes_bytes = pl.off_drow - pl.off_codes;
     size_t sd_bytes = align_up(sizeof(SeqDesc) * count, 256);

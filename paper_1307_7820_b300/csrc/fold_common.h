@@ -20,13 +20,19 @@ constexpr int kPadCode = 4;                     // padding base: pairs with noth
 constexpr int kTraceWords = 10;                 // 64-bit words per task trace record
 
 enum Method : int { kTwoVector = 0, kPlain = 1 };
-enum TaskType : int { kTaskNear = 0, kTaskFar = 1 };
+enum TaskType : int { kTaskNear = 0, kTaskFar = 1, kTaskFarStrip = 2 };
 
 // tile edge for a given q (two-vector) or the plain kernel
 __host__ __device__ constexpr int tile_of(int q, int method) {
     return method == kPlain ? 32 : q * (32 / q);
 }
 __host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
+// tiles per STRIP chunk: every lane of a strip chunk handles this many columns
+// (two-vector: 4 while a tile has at most 4 groups, so the per-group column
+// features of all 4 columns stay in registers; else 2)
+__host__ __device__ constexpr int strip_of(int q, int method) {
+    return method == kPlain ? 2 : (tile_of(q, method) / q <= 4 ? 4 : 2);
+}
 
 // Task word layout (int4): x = sequence index; y = type<<28 | I<<14 | J;
 // NEAR: z = number of FAR chunks that feed the tile; FAR: z = Ka, w = Kb

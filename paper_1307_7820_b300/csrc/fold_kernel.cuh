@@ -106,6 +106,9 @@ struct __align__(16) WarpScratch {
     static constexpr int LR = PL ? 32 : 1;         // plain: late-block row strips
     static constexpr int LF = PL ? 1 : T;          // two-vector: late-block row features
     int2 rf[G][32];                    // FAR staging (two-vector): (A, h-row byte offset)
+    static constexpr int SS = strip_of(Q, M);
+    uint32_t scv[PL ? 1 : G][PL ? 1 : SS + SS / 2][32];  // STRIP staging (two-vector): per group, the
+                                       // lane's column bits for SS columns and SS/2 packed base pairs
     alignas(16) int16_t rows[LR][32];  // FAR staging (plain): row strips (uint4 access)
     alignas(16) int16_t lrow[2][LR][32];  // NEAR late blocks (plain): rows of tiles (I,J-1), (I,I+1)
     alignas(16) uint32_t colpk[PL ? 16 : 1][32];  // NEAR (plain): (D(IT+2m+1,j), D(IT+2m+2,j)) pairs, per lane
@@ -138,6 +141,8 @@ struct ScratchChecks {
 template <int Q, int M>
 __host__ __device__ constexpr size_t smem_bytes_for() {
     static_assert(ScratchChecks<Q, M>::ok, "");
+    static_assert((size_t)round_up(Cfg<Q, M>::RBYTES, 128) + (size_t)kWarpsPerCta * sizeof(WarpScratch<Q, M>) <= 227 * 1024,
+                  "R table plus per-warp scratch must fit the 227 KB per-block shared memory of sm_103a");
     return (size_t)round_up(Cfg<Q, M>::RBYTES, 128) + (size_t)kWarpsPerCta * sizeof(WarpScratch<Q, M>);
 }
 
@@ -337,6 +342,195 @@ __device__ __forceinline__ long long run_far(const FoldParams &P, const SeqDesc 
     return tdone;
 }
 
+// ---------------------------------------------------------------- STRIP chunks
+// Two-vector strip: S tiles (I, J0..J0+S-1) at once, lane = column c of each.
+// For every (row, group) the warp-uniform row feature (A duplicated into both
+// 16-bit halves, h-row offset) is one broadcast load that serves S lookups;
+// two columns share one packed 16x2 accumulator (A + B + R <= n/2 < 2^15, so
+// the halves never carry into each other).
+template <int Q, int S>
+__device__ __forceinline__ void far_strip_tv(const FoldParams &P, const SeqDesc &sd, int I, int J0, int Seff, int Ka,
+                                             int Kb, unsigned (&m2)[S / 2][Cfg<Q, kTwoVector>::T],
+                                             WarpScratch<Q, kTwoVector> &ws, const uint8_t *Rs, int lane) {
+    using C = Cfg<Q, kTwoVector>;
+    constexpr int T = C::T, G = C::G;
+    const int Np = sd.Np, NG = Np / Q;
+    const uint32_t *RF = P.rf + sd.rf_off;
+    const uint32_t *CF = P.cf + sd.cf_off;
+    const bool lv = lane < T;
+    uint32_t cfn[S][G], rfn[G];
+#pragma unroll
+    for (int gl = 0; gl < G; ++gl) {
+        const int g = Ka * G + gl;
+#pragma unroll
+        for (int s = 0; s < S; ++s) cfn[s][gl] = (lv && s < Seff) ? __ldcg(CF + (size_t)g * Np + (J0 + s) * T + lane) : 0u;
+        rfn[gl] = lv ? __ldcg(RF + (size_t)(I * T + lane) * NG + g) : 0u;
+    }
+    for (int K = Ka; K <= Kb; ++K) {
+#pragma unroll
+        for (int gl = 0; gl < G; ++gl) {
+#pragma unroll
+            for (int s2 = 0; s2 < S; ++s2) ws.scv[gl][s2][lane] = cfn[s2][gl] & C::BMASK;
+#pragma unroll
+            for (int p2 = 0; p2 < S / 2; ++p2)
+                ws.scv[gl][S + p2][lane] = (cfn[2 * p2][gl] >> 16) | (cfn[2 * p2 + 1][gl] & 0xffff0000u);
+            ws.rf[gl][lane] = make_int2((int)((rfn[gl] >> 16) * 0x10001u), hrow_offset<Q>((int)(rfn[gl] & C::BMASK)));
+        }
+        if (K < Kb) {   // prefetch the next block
+#pragma unroll
+            for (int gl = 0; gl < G; ++gl) {
+                const int g = (K + 1) * G + gl;
+#pragma unroll
+                for (int s2 = 0; s2 < S; ++s2)
+                    cfn[s2][gl] = (lv && s2 < Seff) ? __ldcg(CF + (size_t)g * Np + (J0 + s2) * T + lane) : 0u;
+                rfn[gl] = lv ? __ldcg(RF + (size_t)(I * T + lane) * NG + g) : 0u;
+            }
+        }
+        __syncwarp();
+        // one group at a time (a runtime loop keeps the live register set small)
+#pragma unroll 1
+        for (int gl = 0; gl < G; ++gl) {
+            int cv[S];
+            unsigned b2[S / 2];
+#pragma unroll
+            for (int s2 = 0; s2 < S; ++s2) cv[s2] = (int)ws.scv[gl][s2][lane];
+#pragma unroll
+            for (int p2 = 0; p2 < S / 2; ++p2) b2[p2] = ws.scv[gl][S + p2][lane];
+#pragma unroll
+            for (int r = 0; r < T; ++r) {
+                const int2 f = ws.rf[gl][r];
+#pragma unroll
+                for (int p2 = 0; p2 < S / 2; ++p2) {
+                    const unsigned v0 = (unsigned)rlookup<Q>(Rs, f.y, cv[2 * p2]);
+                    const unsigned v1 = (unsigned)rlookup<Q>(Rs, f.y, cv[2 * p2 + 1]);
+                    const unsigned t = (unsigned)f.x + b2[p2] + (v1 * 65536u + v0);
+                    m2[p2][r] = __vmaxs2(m2[p2][r], t);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Plain strip: S tiles at once; the row strip of tile (I,K) is staged once in
+// shared memory and serves the S columns of every lane.
+template <int S>
+__device__ __forceinline__ void far_strip_plain(const FoldParams &P, const SeqDesc &sd, int I, int J0, int Seff, int Ka,
+                                                int Kb, unsigned (&acc)[S][32], WarpScratch<8, kPlain> &ws, int lane) {
+    constexpr int T = 32;
+    const int Np = sd.Np, PC = sd.PC;
+    const int16_t *Drow = P.drow + sd.drow_off;
+    const int16_t *Dcol = P.dcol + sd.dcol_off;
+    uint4 rown[4];
+    uint4 coln[S][4];
+    auto load = [&](int K) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(Drow + (size_t)(I * T + lane) * Np + K * T);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) rown[v] = __ldcg(src + v);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const uint4 *cs = reinterpret_cast<const uint4 *>(Dcol + (size_t)((J0 + s) * T + lane) * PC + K * T + 1 + kColOff);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) coln[s][v] = (s < Seff) ? __ldcg(cs + v) : make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
+    load(Ka);
+    for (int K = Ka; K <= Kb; ++K) {
+        unsigned col[S][16];
+        uint4 *dst = reinterpret_cast<uint4 *>(&ws.rows[lane][0]);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) dst[v] = rown[v];
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                col[s][4 * v] = coln[s][v].x; col[s][4 * v + 1] = coln[s][v].y;
+                col[s][4 * v + 2] = coln[s][v].z; col[s][4 * v + 3] = coln[s][v].w;
+            }
+        if (K < Kb) load(K + 1);
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < T; ++r) {
+            const uint4 *rw = reinterpret_cast<const uint4 *>(&ws.rows[r][0]);
+            const uint4 a0 = rw[0], a1 = rw[1], a2 = rw[2], a3 = rw[3];
+            const unsigned aw[16] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w,
+                                     a2.x, a2.y, a2.z, a2.w, a3.x, a3.y, a3.z, a3.w};
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                unsigned x = acc[s][r];
+#pragma unroll
+                for (int w = 0; w < 16; ++w) x = __viaddmax_s16x2(aw[w], col[s][w], x);
+                acc[s][r] = x;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int Q, int M>
+__device__ __forceinline__ long long run_far_strip(const FoldParams &P, const SeqDesc &sd, int I, int J0, int Ka,
+                                                   int Kb, WarpScratch<Q, M> &ws, const uint8_t *Rs, int lane,
+                                                   long long *tdeps) {
+    constexpr int T = Cfg<Q, M>::T;
+    constexpr int S = strip_of(Q, M);
+    const int NT = sd.NT;
+    int *flags = P.flags + sd.flag_off;
+    const int Seff = min(S, NT - J0);
+    const int Jl = J0 + Seff - 1;
+    if (Seff < 1 || Kb < Ka || Ka < I + 2 || Kb > J0 - 2) {
+        if (lane == 0) atomicCAS(P.error, 0, kErrBadTask);
+        return 0;
+    }
+    if (!warp_wait_geq(flags + I * NT + Kb, 1, P, lane)) return 0;
+    if (!warp_wait_geq(flags + Ka * NT + Jl, 1, P, lane)) return 0;
+    if (Jl - I >= kRing && !warp_wait_geq(flags + I * NT + (Jl - kRing), 1, P, lane)) return 0;
+    if (P.trace) tdeps[0] = (long long)gtimer();
+    long long tdone = 0;
+    if constexpr (M == kTwoVector) {
+        unsigned m2[S / 2][T];
+#pragma unroll
+        for (int p2 = 0; p2 < S / 2; ++p2)
+#pragma unroll
+            for (int r = 0; r < T; ++r) m2[p2][r] = 0u;
+        far_strip_tv<Q, S>(P, sd, I, J0, Seff, Ka, Kb, m2, ws, Rs, lane);
+        if (P.trace) tdone = (long long)gtimer();
+        if (lane < T) {
+#pragma unroll
+            for (int s2 = 0; s2 < S; ++s2) {
+                if (s2 >= Seff) continue;
+                int *slot = P.pring + sd.p_off + ((size_t)((J0 + s2 - I) % kRing) * NT + I) * (T * T);
+#pragma unroll
+                for (int r = 0; r < T; ++r) {
+                    const int v = (s2 & 1) ? (int)(m2[s2 / 2][r] >> 16) : (int)(m2[s2 / 2][r] & 0xffffu);
+                    if (v > 0) atomicMax(slot + r * T + lane, v);
+                }
+            }
+        }
+    } else {
+        unsigned acc[S][32];
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2)
+#pragma unroll
+            for (int r = 0; r < 32; ++r) acc[s2][r] = 0u;
+        far_strip_plain<S>(P, sd, I, J0, Seff, Ka, Kb, acc, ws, lane);
+        if (P.trace) tdone = (long long)gtimer();
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2) {
+            if (s2 >= Seff) continue;
+            int *slot = P.pring + sd.p_off + ((size_t)((J0 + s2 - I) % kRing) * NT + I) * (T * T);
+#pragma unroll
+            for (int r = 0; r < T; ++r) {
+                const int v = hmax2(acc[s2][r]);
+                if (v > 0) atomicMax(slot + r * T + lane, v);
+            }
+        }
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane < Seff) atomicAdd(P.cnt + sd.cnt_off + I * NT + J0 + lane, 1);
+    return tdone;
+}
+
 // ---------------------------------------------------------------- NEAR task
 template <int Q, int M>
 __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc &sd, int I, int J, int nfar,
@@ -496,6 +690,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     int *slot = P.pring + sd.p_off + ((size_t)(t % kRing) * NT + I) * (T * T);
     if (nfar > 0) {
         if (!warp_wait_geq(P.cnt + sd.cnt_off + I * NT + J, nfar, P, lane)) return 0;
+        if (P.trace) tdeps[1] = (long long)gtimer();
 #pragma unroll
         for (int r = 0; r < T; ++r) acc[r] = valid ? __ldcg(slot + r * T + c) : 0;
     } else {
@@ -656,8 +851,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         // tile's own column D(IT+c'+1, j), valid for r <= c' < c
 #pragma unroll 1
         for (int r = T - 1; r >= 0; --r) {
-            if (r == T / 2 && P.trace) tdeps[1] = (long long)gtimer();
-            const int pb = (int)((pbits >> r) & 1u);
+                const int pb = (int)((pbits >> r) & 1u);
             int bl = __shfl_up_sync(FULL, below, 1);
             bl = (c == 0) ? 0 : bl;
             int y = (c > r) ? pb + bl : (c == r ? 0 : kNeg16);
@@ -695,8 +889,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         int yold = old_terms(T - 1);
 #pragma unroll 1
         for (int r = T - 1; r >= 0; --r) {
-            if (r == T / 2 && P.trace) tdeps[1] = (long long)gtimer();
-            const int pb = (int)((pbits >> r) & 1u);
+                const int pb = (int)((pbits >> r) & 1u);
             // D(i+1, j-1): lane c-1's previous row; lane 0 reads the left column
             int bl = __shfl_up_sync(FULL, below, 1);
             const int lft = (int)ws.left[r + 1];
@@ -808,8 +1001,10 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
         long long t0 = 0, tdeps[4] = {0, 0, 0, 0};
         if (P.trace && lane == 0) t0 = (long long)gtimer();
         long long tmid;
-        if (task_type(tk.y) == kTaskNear) tmid = run_near<Q, M>(P, sd, I, J, tk.z, ws, Rs, lane, tdeps);
-        else tmid = run_far<Q, M>(P, sd, I, J, tk.z, tk.w, ws, Rs, lane, tdeps);
+        const int ty = task_type(tk.y);
+        if (ty == kTaskNear) tmid = run_near<Q, M>(P, sd, I, J, tk.z, ws, Rs, lane, tdeps);
+        else if (ty == kTaskFar) tmid = run_far<Q, M>(P, sd, I, J, tk.z, tk.w, ws, Rs, lane, tdeps);
+        else tmid = run_far_strip<Q, M>(P, sd, I, J, tk.z, tk.w, ws, Rs, lane, tdeps);
         if (P.trace && lane == 0) {
             long long *rec = P.trace + (size_t)idx * kTraceWords;
             rec[0] = ((long long)(blockIdx.x * kWarpsPerCta + warp) << 32) | (unsigned)idx;

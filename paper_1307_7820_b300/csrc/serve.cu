@@ -315,7 +315,7 @@ int fold_serve_submit(fold_ctx *ctx, const char *seq, int32_t n, uint64_t *ticke
     if (!encode_seq(seq, n, r.codes.data())) return FOLD_EINVAL;
     if (n > 0) {
         int kc = ctx->kc_override > 0 ? ctx->kc_override : kc_auto(r.NT);
-        build_schedule_steps(r.NT, kc, r.tasks, r.step_begin);
+        build_schedule_steps(r.NT, kc, strip_of(ctx->q, ctx->method), r.tasks, r.step_begin);
     }
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->reqs.size() >= kMaxQueued) return FOLD_EAGAIN;

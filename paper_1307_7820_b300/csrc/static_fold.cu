@@ -94,7 +94,7 @@ extern "C" int fold_score_static(const uint8_t *d_codes, int32_t n, uint16_t pai
     int32_t len = n;
     Plan pl = make_plan(&len, 1, kStaticQ, kTwoVector);
     std::vector<int4> tasks;
-    if (n > 0) build_schedule(pl.NTs, kc_auto(pl.NTs[0]), tasks);
+    if (n > 0) build_schedule(pl.NTs, kc_auto(pl.NTs[0]), strip_of(kStaticQ, kTwoVector), tasks);
     const size_t o_sd = 2 * kStaticRBytes;
     const size_t o_tasks = st_align(o_sd + sizeof(SeqDesc));
     const size_t o_plan = st_align(o_tasks + tasks.size() * sizeof(int4));

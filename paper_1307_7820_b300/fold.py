@@ -31,7 +31,7 @@ ABI_SYMBOLS = (
     "fold_init", "fold_destroy", "fold_strerror", "fold_set_option", "fold_get_option", "fold_rtable",
     "fold_score", "fold_workspace_bytes", "fold_score_dev", "fold_batch",
     "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop", "fold_trace_copy",
-    "fold_score_static",
+    "fold_score_static", "fold_schedule_check",
 )
 
 
@@ -83,6 +83,8 @@ def lib():
     L.fold_trace_copy.argtypes = [vp, vp, i64]
     L.fold_score_static.argtypes = [vp, i32, u16, vp, vp, vp]
     L.fold_score_static.restype = ctypes.c_int
+    L.fold_schedule_check.argtypes = [i32, ctypes.c_int, ctypes.c_int, i32]
+    L.fold_schedule_check.restype = ctypes.c_int
     L.fold_trace_copy.restype = i64
     for name in ("fold_set_option", "fold_get_option", "fold_rtable", "fold_score", "fold_score_dev", "fold_batch",
                  "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop"):
@@ -182,6 +184,11 @@ def fold_score_static(d_codes: int | None, n: int, pair_mask: int, d_max_pairs: 
                       d_D_out: int | None = None, stream: int | None = None) -> None:
     """Allocation-free fold of up to FOLD_STATIC_MAX_N bases (device pointers as ints)."""
     _check(lib().fold_score_static(d_codes, n, pair_mask, d_max_pairs, d_D_out, stream), "fold_score_static")
+
+
+def fold_schedule_check(n: int, q: int = 8, method: int = FOLD_METHOD_TWO_VECTOR, kchunk: int = 0) -> int:
+    """0 if the task list for length n is valid (host only, no GPU)."""
+    return lib().fold_schedule_check(n, q, method, kchunk)
 
 
 def fold_serve_start(ctx: int, budget_bytes: int, max_inflight: int = 4096) -> None:
