@@ -77,7 +77,9 @@ enum fold_option {
                                     expire and the call returns FOLD_ETIMEOUT; 0 = off (default) */
     FOLD_OPT_TIMING = 9,      /* 1 = record CUDA events around every persistent fold kernel launch */
     FOLD_OPT_KERNEL_NS = 10,  /* read-only: duration of the last timed fold kernel in ns (waits for it) */
-    FOLD_OPT_TRACE = 11       /* 1 = record per-task timestamps (see fold_trace_copy); 0 = off */
+    FOLD_OPT_TRACE = 11,      /* 1 = record per-task timestamps (see fold_trace_copy); 0 = off */
+    FOLD_OPT_NEAR_CTAS = 12   /* single folds: CTAs that run only tile tasks while the others run only
+                                 middle-block chunks; -1 = automatic (default), 0 = one shared queue */
 };
 
 /* One record per task of the last traced persistent launch. */

@@ -85,6 +85,9 @@ FoldParams make_params(const fold_ctx *ctx, const Plan &pl, uint8_t *ws, const i
     p.ntasks = ntasks;
     p.queue_head = reinterpret_cast<int *>(ws + pl.off_control);
     p.error = reinterpret_cast<int *>(ws + pl.off_control) + 1;
+    p.queue_head_far = reinterpret_cast<int *>(ws + pl.off_control) + 2;
+    p.nnear = 0;
+    p.near_ctas = 0;
     p.seqs = d_sd;
     p.codes = ws + pl.off_codes;
     p.drow = reinterpret_cast<int16_t *>(ws + pl.off_drow);
@@ -106,6 +109,41 @@ int grid_for(fold_ctx *ctx) {
     int bps = fold_blocks_per_sm(ctx->q, ctx->method);
     if (bps < 1) bps = 1;
     return ctx->sm_count * bps;
+}
+
+// Tile-only CTAs for a single fold.  Tile tasks form the critical path (one
+// per tile diagonal, about 13 us each); chunk warps on the same SM slow them
+// down by competing for issue slots and shared memory.  Dedicated SMs pay off
+// when the chunk work is of the same order as that path: with much less there
+// is little contention to remove, with much more the fold is bound by chunk
+// throughput and every SM taken from it costs time.  The model compares the
+// chunk work at the measured rates (two-vector about 4e9 lookups per ms, plain
+// about 2e10 split points per ms, on 148 SMs) with the path.  When it splits,
+// the tile CTAs get enough warps for a whole tile diagonal (kWarpsPerCta tiles
+// per CTA), at most a sixth of the grid.  0 means one shared queue.
+int near_ctas_for(fold_ctx *ctx, int NT, int grid) {
+    if (ctx->near_ctas_opt >= 0) return std::min(ctx->near_ctas_opt, grid - 1);
+    if (NT < 8 || grid < 12) return 0;
+    const double n = (double)NT * tile_of(ctx->q, ctx->method);
+    const double sm_scale = 148.0 / std::max(1, ctx->sm_count);
+    const double work_ms = sm_scale * (ctx->method == kTwoVector ? n * n * n / (6.0 * ctx->q) / 4.0e9
+                                                                  : n * n * n / 6.0 / 2.0e10);
+    const double path_ms = NT * 0.013;
+    const double rho = work_ms / path_ms;
+    if (rho < 0.15 || rho > 1.5) return 0;
+    return std::max(2, std::min((NT + kWarpsPerCta - 1) / kWarpsPerCta, grid / 6));
+}
+
+// Reorders a task list into [tile tasks | chunk tasks], keeping the list order
+// inside each part; returns the number of tile tasks.
+int split_queues(std::vector<int4> &tasks) {
+    std::vector<int4> near, far;
+    near.reserve(tasks.size());
+    for (const int4 &t : tasks) (task_type(t.y) == kTaskNear ? near : far).push_back(t);
+    const int nn = (int)near.size();
+    near.insert(near.end(), far.begin(), far.end());
+    tasks.swap(near);
+    return nn;
 }
 
 int status_from_cuda(cudaError_t e) {
@@ -182,10 +220,13 @@ bool encode_seq(const char *seq, int n, uint8_t *out) {
 }
 
 // Cached device schedule + descriptor for a single sequence of length n.
-int single_schedule(fold_ctx *ctx, int n, const Plan &pl, const int4 **tasks, int *ntasks, const SeqDesc **d_sd) {
+int single_schedule(fold_ctx *ctx, int n, const Plan &pl, const int4 **tasks, int *ntasks, int *nnear,
+                    const SeqDesc **d_sd) {
     int NT = pl.NTs[0];
     int kc = ctx->kc_override > 0 ? ctx->kc_override : kc_auto(NT);
-    long long key = ((long long)n << 24) | ((long long)ctx->method << 20) | ((long long)ctx->q << 16) | kc;
+    const int nearc = near_ctas_for(ctx, NT, grid_for(ctx));
+    long long key = ((((long long)n << 24) | ((long long)ctx->method << 20) | ((long long)ctx->q << 16) | kc) << 12) |
+                    (nearc & 0xfff);
     if (ctx->test_drop_task) key = -key - 1;   // separate cache entry for the fault-injection schedule
     auto it = ctx->sched_cache.find(key);
     if (it == ctx->sched_cache.end()) {
@@ -200,6 +241,7 @@ int single_schedule(fold_ctx *ctx, int n, const Plan &pl, const int4 **tasks, in
                 }
         }
         CachedSched cs;
+        cs.nnear = nearc > 0 ? split_queues(tv) : 0;
         cs.ntasks = (int)tv.size();
         size_t bytes = tv.size() * sizeof(int4) + 256 + sizeof(SeqDesc);
         if (cudaMalloc(&cs.dev, bytes) != cudaSuccess) { cudaGetLastError(); return FOLD_ENOMEM; }
@@ -213,6 +255,7 @@ int single_schedule(fold_ctx *ctx, int n, const Plan &pl, const int4 **tasks, in
     }
     *tasks = it->second.d_tasks;
     *ntasks = it->second.ntasks;
+    *nnear = it->second.nnear;
     *d_sd = it->second.d_sd;
     return FOLD_OK;
 }
@@ -227,13 +270,17 @@ int enqueue_single(fold_ctx *ctx, const uint8_t *d_codes, int n, uint8_t *ws, si
     if (e != cudaSuccess) return status_from_cuda(e);
     if (n >= 1) {
         const int4 *tasks;
-        int ntasks;
+        int ntasks, nnear;
         const SeqDesc *d_sd;
-        int rc = single_schedule(ctx, n, pl, &tasks, &ntasks, &d_sd);
+        int rc = single_schedule(ctx, n, pl, &tasks, &ntasks, &nnear, &d_sd);
         if (rc) return rc;
         e = launch_pad_codes(d_codes, n, pl.sd[0].Np, ws + pl.off_codes, st);
         if (e != cudaSuccess) return status_from_cuda(e);
         FoldParams p = make_params(ctx, pl, ws, tasks, ntasks, d_sd);
+        if (nnear > 0) {
+            p.nnear = nnear;
+            p.near_ctas = near_ctas_for(ctx, pl.NTs[0], grid_for(ctx));
+        }
         e = launch_fold_instrumented(ctx, p, st);
         if (e != cudaSuccess) return status_from_cuda(e);
         ctx->launches += 2;
@@ -363,6 +410,10 @@ int fold_set_option(fold_ctx *ctx, int option, int64_t value) {
             if (value < 0 || value > 1) return FOLD_EINVAL;
             ctx->trace = (int)value;
             return FOLD_OK;
+        case FOLD_OPT_NEAR_CTAS:
+            if (value < -1 || value > 4096) return FOLD_EINVAL;
+            ctx->near_ctas_opt = (int)value;
+            return FOLD_OK;
     }
     return FOLD_EINVAL;
 }
@@ -380,6 +431,7 @@ int fold_get_option(fold_ctx *ctx, int option, int64_t *value) {
         case FOLD_OPT_TEST_DROP_TASK: *value = ctx->test_drop_task; return FOLD_OK;
         case FOLD_OPT_TIMING: *value = ctx->timing; return FOLD_OK;
         case FOLD_OPT_TRACE: *value = ctx->trace; return FOLD_OK;
+        case FOLD_OPT_NEAR_CTAS: *value = ctx->near_ctas_opt; return FOLD_OK;
         case FOLD_OPT_KERNEL_NS: {
             if (!ctx->ev_pending) { *value = 0; return FOLD_OK; }
             float ms = 0.f;

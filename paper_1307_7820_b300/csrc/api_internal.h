@@ -19,6 +19,7 @@ struct CachedSched {
     SeqDesc *d_sd = nullptr;
     int4 *d_tasks = nullptr;
     int ntasks = 0;
+    int nnear = 0;             // > 0: tasks are split [tile tasks | chunk tasks]
 };
 
 // Workspace layout of a set of sequences (byte offsets into one buffer).
@@ -46,6 +47,7 @@ struct fold_ctx {
     int kc_override = 0;
     long long timeout_ms = 5000;
     int test_drop_task = 0;
+    int near_ctas_opt = -1;    // -1 automatic, 0 one shared queue, k > 0 k tile-only CTAs
     cudaStream_t stream = nullptr;
     uint8_t *d_rcanon = nullptr;
     uint8_t *d_rpacked_buf = nullptr;
@@ -72,6 +74,8 @@ int grid_for(fold_ctx *ctx);
 int kc_auto(int NT);
 int status_from_cuda(cudaError_t e);
 cudaError_t launch_fold_instrumented(fold_ctx *ctx, FoldParams &p, cudaStream_t st);
+int near_ctas_for(fold_ctx *ctx, int NT, int grid);
+int split_queues(std::vector<int4> &tasks);
 bool encode_seq(const char *seq, int n, uint8_t *out);
 int ensure_buf(DevBuf &b, size_t bytes);
 int ensure_host(HostBuf &b, size_t bytes);

@@ -63,7 +63,13 @@ struct SeqDesc {
 struct FoldParams {
     const int4 *tasks;
     int ntasks;
-    int *queue_head;          // next task index
+    int *queue_head;          // next task index (tile tasks when the queues are split)
+    // split queues: tasks[0, nnear) are the tile (NEAR) tasks and tasks[nnear, ntasks) the chunk
+    // tasks, each part in list order; CTAs with blockIdx.x < near_ctas take only tile tasks (through
+    // queue_head), the others only chunk tasks (through queue_head_far).  near_ctas == 0: one queue.
+    int nnear;
+    int near_ctas;
+    int *queue_head_far;
     int *error;               // first error code (0 = none) and where
     const SeqDesc *seqs;
     const uint8_t *codes;

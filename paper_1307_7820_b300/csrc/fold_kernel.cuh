@@ -989,11 +989,16 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
     __syncthreads();
     WarpScratch<Q, M> &ws =
         *reinterpret_cast<WarpScratch<Q, M> *>(smem + round_up(C::RBYTES, 128) + warp * sizeof(WarpScratch<Q, M>));
+    const bool split = P.near_ctas > 0;
+    const bool far_role = split && (int)blockIdx.x >= P.near_ctas;
+    int *qhead = far_role ? P.queue_head_far : P.queue_head;
+    const int qbase = far_role ? P.nnear : 0;
+    const int qlimit = (split && !far_role) ? P.nnear : P.ntasks;
     for (;;) {
         int idx = 0;
-        if (lane == 0) idx = atomicAdd(P.queue_head, 1);
+        if (lane == 0) idx = qbase + atomicAdd(qhead, 1);
         idx = __shfl_sync(FULL, idx, 0);
-        if (idx >= P.ntasks) break;
+        if (idx >= qlimit) break;
         if (*(volatile int *)P.error != 0) break;
         const int4 tk = P.tasks[idx];
         const SeqDesc sd = P.seqs[tk.x];

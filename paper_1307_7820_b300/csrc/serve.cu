@@ -218,6 +218,9 @@ static void serve_loop(ServeState *S) {
         p.ntasks = (int)tasks.size();
         p.queue_head = reinterpret_cast<int *>(d);
         p.error = reinterpret_cast<int *>(d) + 1;
+        p.queue_head_far = reinterpret_cast<int *>(d) + 2;
+        p.nnear = 0;
+        p.near_ctas = 0;
         p.seqs = reinterpret_cast<const SeqDesc *>(d + o_sd);
         p.codes = S->arena_base;
         p.drow = reinterpret_cast<int16_t *>(S->arena_base);

@@ -119,6 +119,9 @@ extern "C" int fold_score_static(const uint8_t *d_codes, int32_t n, uint16_t pai
         p.ntasks = (int)tasks.size();
         p.queue_head = reinterpret_cast<int *>(ws + pl.off_control);
         p.error = reinterpret_cast<int *>(ws + pl.off_control) + 1;
+        p.queue_head_far = reinterpret_cast<int *>(ws + pl.off_control) + 2;
+        p.nnear = 0;
+        p.near_ctas = 0;
         p.seqs = reinterpret_cast<const SeqDesc *>(base + o_sd);
         p.codes = ws + pl.off_codes;
         p.drow = reinterpret_cast<int16_t *>(ws + pl.off_drow);
