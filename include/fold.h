@@ -78,8 +78,11 @@ enum fold_option {
     FOLD_OPT_TIMING = 9,      /* 1 = record CUDA events around every persistent fold kernel launch */
     FOLD_OPT_KERNEL_NS = 10,  /* read-only: duration of the last timed fold kernel in ns (waits for it) */
     FOLD_OPT_TRACE = 11,      /* 1 = record per-task timestamps (see fold_trace_copy); 0 = off */
-    FOLD_OPT_NEAR_CTAS = 12   /* single folds: CTAs that run only tile tasks while the others run only
+    FOLD_OPT_NEAR_CTAS = 12,  /* single folds: CTAs that run only tile tasks while the others run only
                                  middle-block chunks; -1 = automatic (default), 0 = one shared queue */
+    FOLD_OPT_COLUMNS = 13     /* with tile-only CTAs: each warp owns one tile column and computes it
+                                 bottom-up (needs ceil(n_tiles / v) tile CTAs); -1 = automatic
+                                 (default, v = 8), 0 = off, v = 1..8 = on, v columns per tile CTA */
 };
 
 /* One record per task of the last traced persistent launch. */

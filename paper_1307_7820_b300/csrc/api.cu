@@ -111,27 +111,74 @@ int grid_for(fold_ctx *ctx) {
     return ctx->sm_count * bps;
 }
 
-// Tile-only CTAs for a single fold.  Tile tasks form the critical path (one
-// per tile diagonal, about 13 us each); chunk warps on the same SM slow them
-// down by competing for issue slots and shared memory.  Dedicated SMs pay off
-// when the chunk work is of the same order as that path: with much less there
-// is little contention to remove, with much more the fold is bound by chunk
-// throughput and every SM taken from it costs time.  The model compares the
-// chunk work at the measured rates (two-vector about 4e9 lookups per ms, plain
-// about 2e10 split points per ms, on 148 SMs) with the path.  When it splits,
-// the tile CTAs get enough warps for a whole tile diagonal (kWarpsPerCta tiles
-// per CTA), at most a sixth of the grid.  0 means one shared queue.
-int near_ctas_for(fold_ctx *ctx, int NT, int grid) {
-    if (ctx->near_ctas_opt >= 0) return std::min(ctx->near_ctas_opt, grid - 1);
-    if (NT < 8 || grid < 12) return 0;
+// Work split of a single fold.  Tile tasks form the critical path (one per tile diagonal, each
+// waiting for its neighbours); chunk tasks are throughput work.  Chunk warps on an SM slow the
+// tile warps there (issue slots, shared memory), so tile tasks may get SMs of their own.  The
+// candidate layouts, with the measured cost of one tile-diagonal step (B300, q = 8):
+//   one shared queue                          about 16.5 us, chunks on every SM
+//   tile-only CTAs taking tile tasks          about 13.8 us, chunks on the other SMs
+//   column mode, 4 columns per tile CTA       about 13.0 us
+//   column mode, 8 columns per tile CTA       about 15.0 us
+// Column mode gives every tile column a warp of its own that computes it bottom-up: a tile's
+// bottom neighbour is the warp's previous tile, and its left neighbour comes through shared memory
+// unless it is the first column of its CTA.  A layout's time is modelled as the larger of the path
+// (NT steps) and the chunk work at the measured rates (two-vector about 4e9 lookups per ms, plain
+// about 2e10 split points per ms, on 148 SMs) spread over the SMs left to chunks; the fastest wins.
+// The options force a layout: FOLD_OPT_NEAR_CTAS (0 = one queue, k = k tile CTAs) and
+// FOLD_OPT_COLUMNS (0 = no column mode, v = column mode with v columns per tile CTA).
+SplitPlan plan_split(fold_ctx *ctx, int NT, int grid, bool layout_ok) {
+    SplitPlan sp;
+    const int nopt = ctx->near_ctas_opt, copt = ctx->columns_opt;
+    if (nopt == 0 || NT < 2 || grid < 2) return sp;
+    auto ceil_div = [](int a, int b) { return (a + b - 1) / b; };
+    auto column = [&](int cpc, int near) -> bool {
+        near = std::max(near, ceil_div(NT, cpc));
+        if (!layout_ok || near > grid - 1) return false;
+        sp.near_ctas = near;
+        sp.col_mode = 1;
+        sp.cpc = cpc;
+        return true;
+    };
+    if (nopt > 0) {                            // forced tile CTAs
+        const int near = std::min(nopt, grid - 1);
+        if (copt >= 1 && column(copt, near)) return sp;
+        if (copt == -1 && near >= ceil_div(NT, kWarpsPerCta) && column(kWarpsPerCta, near)) return sp;
+        sp.near_ctas = near;
+        return sp;
+    }
+    if (copt >= 1) {                           // forced column mode
+        column(copt, 0);
+        return sp;
+    }
+    if (NT < 8 || grid < 12) return sp;
     const double n = (double)NT * tile_of(ctx->q, ctx->method);
-    const double sm_scale = 148.0 / std::max(1, ctx->sm_count);
-    const double work_ms = sm_scale * (ctx->method == kTwoVector ? n * n * n / (6.0 * ctx->q) / 4.0e9
-                                                                  : n * n * n / 6.0 / 2.0e10);
-    const double path_ms = NT * 0.013;
-    const double rho = work_ms / path_ms;
-    if (rho < 0.15 || rho > 1.5) return 0;
-    return std::max(2, std::min((NT + kWarpsPerCta - 1) / kWarpsPerCta, grid / 6));
+    const double work_ms = (148.0 / std::max(1, ctx->sm_count)) *
+                           (ctx->method == kTwoVector ? n * n * n / (6.0 * ctx->q) / 4.0e9 : n * n * n / 6.0 / 2.0e10);
+    auto model = [&](double step_us, int near) {
+        return std::max(NT * step_us * 1e-3, work_ms * grid / std::max(1, grid - near));
+    };
+    double best = model(16.5, 0);
+    const int near_split = std::max(2, std::min(ceil_div(NT, kWarpsPerCta), grid / 6));
+    const double split = model(13.8, near_split);
+    if (split < best) {
+        best = split;
+        sp.near_ctas = near_split;
+    }
+    if (copt == 0 || !layout_ok) return sp;
+    const int cands[2] = {4, 8};
+    const double steps[2] = {13.0, 15.0};
+    for (int k = 0; k < 2; ++k) {
+        const int near = ceil_div(NT, cands[k]);
+        if (near > grid / 3) continue;
+        const double m = model(steps[k], near);
+        if (m < best) {
+            best = m;
+            sp.near_ctas = near;
+            sp.col_mode = 1;
+            sp.cpc = cands[k];
+        }
+    }
+    return sp;
 }
 
 // Reorders a task list into [tile tasks | chunk tasks], keeping the list order
@@ -221,10 +268,11 @@ bool encode_seq(const char *seq, int n, uint8_t *out) {
 
 // Cached device schedule + descriptor for a single sequence of length n.
 int single_schedule(fold_ctx *ctx, int n, const Plan &pl, const int4 **tasks, int *ntasks, int *nnear,
-                    const SeqDesc **d_sd) {
+                    bool *layout_ok, const SeqDesc **d_sd) {
     int NT = pl.NTs[0];
     int kc = ctx->kc_override > 0 ? ctx->kc_override : kc_auto(NT);
-    const int nearc = near_ctas_for(ctx, NT, grid_for(ctx));
+    // the split list is the same for every split layout; layout_ok is assumed for the choice here
+    const int nearc = plan_split(ctx, NT, grid_for(ctx), true).near_ctas;
     long long key = ((((long long)n << 24) | ((long long)ctx->method << 20) | ((long long)ctx->q << 16) | kc) << 12) |
                     (nearc & 0xfff);
     if (ctx->test_drop_task) key = -key - 1;   // separate cache entry for the fault-injection schedule
@@ -243,6 +291,11 @@ int single_schedule(fold_ctx *ctx, int n, const Plan &pl, const int4 **tasks, in
         CachedSched cs;
         cs.nnear = nearc > 0 ? split_queues(tv) : 0;
         cs.ntasks = (int)tv.size();
+        // column mode finds tile (I, I+t) at position t*NT - t(t-1)/2 + I of the tile tasks
+        cs.layout_ok = cs.nnear == NT * (NT + 1) / 2;
+        for (int t = 0, k = 0; cs.layout_ok && t < NT; ++t)
+            for (int I = 0; I + t < NT; ++I, ++k)
+                if (tv[k].y != task_pack(kTaskNear, I, I + t)) { cs.layout_ok = false; break; }
         size_t bytes = tv.size() * sizeof(int4) + 256 + sizeof(SeqDesc);
         if (cudaMalloc(&cs.dev, bytes) != cudaSuccess) { cudaGetLastError(); return FOLD_ENOMEM; }
         cs.d_sd = reinterpret_cast<SeqDesc *>(cs.dev);
@@ -256,6 +309,7 @@ int single_schedule(fold_ctx *ctx, int n, const Plan &pl, const int4 **tasks, in
     *tasks = it->second.d_tasks;
     *ntasks = it->second.ntasks;
     *nnear = it->second.nnear;
+    *layout_ok = it->second.layout_ok;
     *d_sd = it->second.d_sd;
     return FOLD_OK;
 }
@@ -271,15 +325,19 @@ int enqueue_single(fold_ctx *ctx, const uint8_t *d_codes, int n, uint8_t *ws, si
     if (n >= 1) {
         const int4 *tasks;
         int ntasks, nnear;
+        bool layout_ok;
         const SeqDesc *d_sd;
-        int rc = single_schedule(ctx, n, pl, &tasks, &ntasks, &nnear, &d_sd);
+        int rc = single_schedule(ctx, n, pl, &tasks, &ntasks, &nnear, &layout_ok, &d_sd);
         if (rc) return rc;
         e = launch_pad_codes(d_codes, n, pl.sd[0].Np, ws + pl.off_codes, st);
         if (e != cudaSuccess) return status_from_cuda(e);
         FoldParams p = make_params(ctx, pl, ws, tasks, ntasks, d_sd);
         if (nnear > 0) {
+            const SplitPlan sp = plan_split(ctx, pl.NTs[0], grid_for(ctx), layout_ok);
+            p.col_mode = sp.col_mode;
+            p.cols_per_cta = sp.cpc;
             p.nnear = nnear;
-            p.near_ctas = near_ctas_for(ctx, pl.NTs[0], grid_for(ctx));
+            p.near_ctas = sp.near_ctas;
         }
         e = launch_fold_instrumented(ctx, p, st);
         if (e != cudaSuccess) return status_from_cuda(e);
@@ -414,6 +472,10 @@ int fold_set_option(fold_ctx *ctx, int option, int64_t value) {
             if (value < -1 || value > 4096) return FOLD_EINVAL;
             ctx->near_ctas_opt = (int)value;
             return FOLD_OK;
+        case FOLD_OPT_COLUMNS:
+            if (value < -1 || value > kWarpsPerCta) return FOLD_EINVAL;
+            ctx->columns_opt = (int)value;
+            return FOLD_OK;
     }
     return FOLD_EINVAL;
 }
@@ -432,6 +494,7 @@ int fold_get_option(fold_ctx *ctx, int option, int64_t *value) {
         case FOLD_OPT_TIMING: *value = ctx->timing; return FOLD_OK;
         case FOLD_OPT_TRACE: *value = ctx->trace; return FOLD_OK;
         case FOLD_OPT_NEAR_CTAS: *value = ctx->near_ctas_opt; return FOLD_OK;
+        case FOLD_OPT_COLUMNS: *value = ctx->columns_opt; return FOLD_OK;
         case FOLD_OPT_KERNEL_NS: {
             if (!ctx->ev_pending) { *value = 0; return FOLD_OK; }
             float ms = 0.f;

@@ -20,6 +20,7 @@ struct CachedSched {
     int4 *d_tasks = nullptr;
     int ntasks = 0;
     int nnear = 0;             // > 0: tasks are split [tile tasks | chunk tasks]
+    bool layout_ok = false;    // the tile tasks are in diagonal order, every tile once (column mode)
 };
 
 // Workspace layout of a set of sequences (byte offsets into one buffer).
@@ -48,6 +49,7 @@ struct fold_ctx {
     long long timeout_ms = 5000;
     int test_drop_task = 0;
     int near_ctas_opt = -1;    // -1 automatic, 0 one shared queue, k > 0 k tile-only CTAs
+    int columns_opt = -1;      // -1 automatic, 0 off, v >= 1 column mode with v columns per tile CTA
     cudaStream_t stream = nullptr;
     uint8_t *d_rcanon = nullptr;
     uint8_t *d_rpacked_buf = nullptr;
@@ -74,7 +76,12 @@ int grid_for(fold_ctx *ctx);
 int kc_auto(int NT);
 int status_from_cuda(cudaError_t e);
 cudaError_t launch_fold_instrumented(fold_ctx *ctx, FoldParams &p, cudaStream_t st);
-int near_ctas_for(fold_ctx *ctx, int NT, int grid);
+struct SplitPlan {
+    int near_ctas = 0;   // tile-only CTAs (0: one shared queue)
+    int col_mode = 0;    // 1: column mode
+    int cpc = kWarpsPerCta;   // columns per tile CTA in column mode
+};
+SplitPlan plan_split(fold_ctx *ctx, int NT, int grid, bool layout_ok);
 int split_queues(std::vector<int4> &tasks);
 bool encode_seq(const char *seq, int n, uint8_t *out);
 int ensure_buf(DevBuf &b, size_t bytes);

@@ -70,6 +70,11 @@ struct FoldParams {
     int nnear;
     int near_ctas;
     int *queue_head_far;
+    // column mode (split queues, one sequence): the tile tasks are not taken from the queue; warp w of
+    // tile CTA b owns tile column b * cols_per_cta + w and computes its tiles bottom-up, (J,J) first.
+    // tasks[0, nnear) still lists them (diagonal by diagonal) for their chunk counts.
+    int col_mode;
+    int cols_per_cta;
     int *error;               // first error code (0 = none) and where
     const SeqDesc *seqs;
     const uint8_t *codes;

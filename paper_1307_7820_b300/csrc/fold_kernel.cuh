@@ -46,6 +46,15 @@ static __device__ __forceinline__ int ld_acquire(const int *p) {
 static __device__ __forceinline__ void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+static __device__ __forceinline__ int ld_relaxed(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+static __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+static __device__ __forceinline__ void st_relaxed(int *p, int v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 static __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -84,6 +93,38 @@ static __device__ __forceinline__ bool warp_wait_geq(const int *p, int target, c
     return wait_geq_impl(p, target, P.error, P.timeout_ns, lane);
 }
 
+// shared-memory flags between the warps of one CTA (column mode)
+static __device__ __forceinline__ int ld_acquire_cta(const int *p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared.b32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+    return v;
+}
+static __device__ __forceinline__ void st_release_cta(int *p, int v) {
+    asm volatile("st.release.cta.shared.b32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+// Lane 0 waits (bounded) until the shared word *p >= target; the error word and the clock are
+// checked every 32 polls so that a poll costs one shared load.
+static __device__ __noinline__ bool wait_smem_geq(const int *p, int target, int *error, long long timeout_ns, int lane) {
+    int ok = 1;
+    if (lane == 0 && ld_acquire_cta(p) < target) {
+        const unsigned long long t0 = gtimer();
+        for (unsigned it = 1;; ++it) {
+            if (ld_acquire_cta(p) >= target) break;
+            if ((it & 31u) == 0) {
+                if (*(volatile int *)error != 0) { ok = 0; break; }
+                if ((long long)(gtimer() - t0) > timeout_ns) {
+                    atomicCAS(error, 0, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+    }
+    ok = __shfl_sync(FULL, ok, 0);
+    __syncwarp();
+    return ok != 0;
+}
+
 static __device__ __forceinline__ int lds16(const int16_t *p) { return (int)*p; }
 static __device__ __forceinline__ int ldcg16(const int16_t *p) { return (int)__ldcg(p); }
 
@@ -105,14 +146,23 @@ struct __align__(16) WarpScratch {
     static constexpr bool PL = (M == kPlain);
     static constexpr int LR = PL ? 32 : 1;         // plain: late-block row strips
     static constexpr int LF = PL ? 1 : T;          // two-vector: late-block row features
-    int2 rf[G][32];                    // FAR staging (two-vector): (A, h-row byte offset)
     static constexpr int SS = strip_of(Q, M);
-    uint32_t scv[PL ? 1 : G][PL ? 1 : SS + SS / 2][32];  // STRIP staging (two-vector): per group, the
-                                       // lane's column bits for SS columns and SS/2 packed base pairs
-    alignas(16) int16_t rows[LR][32];  // FAR staging (plain): row strips (uint4 access)
+    union {
+        struct {                       // chunk tasks
+            int2 rf[G][32];            // FAR staging (two-vector): (A, h-row byte offset)
+            uint32_t scv[PL ? 1 : G][PL ? 1 : SS + SS / 2][32];  // STRIP staging (two-vector): per group,
+                                       // the lane's column bits for SS columns and SS/2 packed base pairs
+            alignas(16) int16_t rows[LR][32];  // FAR staging (plain): row strips (uint4 access)
+        };
+        struct {                       // column mode (its warps run no chunk tasks)
+            int16_t tile1[T + 1][33];  // second output buffer: tiles alternate between tile and tile1
+            uint32_t rfo[2][LF][G];    // row features of the last two tiles (two-vector), read by the
+                                       // warp of the next column
+        };
+    };
     alignas(16) int16_t lrow[2][LR][32];  // NEAR late blocks (plain): rows of tiles (I,J-1), (I,I+1)
     alignas(16) uint32_t colpk[PL ? 16 : 1][32];  // NEAR (plain): (D(IT+2m+1,j), D(IT+2m+2,j)) pairs, per lane
-    uint32_t lrf[2][LF][G];            // NEAR late blocks (two-vector): row features of (I,J-1), (I,I+1)
+    alignas(16) uint32_t lrf[2][LF][G];  // NEAR late blocks (two-vector): row features of (I,J-1), (I,I+1)
     uint32_t cbc[G + 1][32];           // NEAR (two-vector): (base << 16 | bits) of the lane's column groups;
                                        // row G takes the stores of rows that complete no group
     static constexpr int DS = PL ? 40 : T + 2;   // row stride (plain reads rows as uint4)
@@ -121,9 +171,10 @@ struct __align__(16) WarpScratch {
     int16_t pm[T][32];                 // far partial max of each row (lane = column)
     alignas(16) int16_t y[2][32];      // closure exchange, double-buffered (read back as uint4)
     int16_t left[T + 2];               // D(IT+m, JT-1)
-    uint8_t rcode[32];                 // codes of the tile's rows
     int16_t tile[T + 1][33];           // output tile; row T holds D((I+1)T, j); 33 columns so every lane's
                                        // index (also lanes >= T) stays inside the array
+    int produced;                      // column mode: tiles of this column published in shared memory
+    int consumed;                      // column mode, written by the next column's warp: tiles it has read
 };
 
 // every vector-accessed member must sit on a 16-byte boundary
@@ -133,6 +184,7 @@ struct ScratchChecks {
     static_assert(offsetof(WS, y) % 16 == 0, "y must be 16-byte aligned");
     static_assert(offsetof(WS, rows) % 16 == 0, "rows must be 16-byte aligned");
     static_assert(offsetof(WS, lrow) % 16 == 0, "lrow must be 16-byte aligned");
+    static_assert(offsetof(WS, lrf) % 16 == 0, "lrf must be 16-byte aligned");
     static_assert(M != kPlain || (offsetof(WS, diag) % 16 == 0 && (WS::DS * 2) % 16 == 0), "diag rows 16-byte aligned");
     static_assert(sizeof(WarpScratch<Q, M>) % 16 == 0, "scratch stride must keep 16-byte alignment");
     static constexpr bool ok = true;
@@ -532,9 +584,26 @@ __device__ __forceinline__ long long run_far_strip(const FoldParams &P, const Se
 }
 
 // ---------------------------------------------------------------- NEAR task
+// Column mode: what the warp owning tile column J carries from tile (I+1,J) to tile (I,J), and the
+// link to the warp of column J-1 when that warp runs in the same CTA.
 template <int Q, int M>
+struct NearCol {
+    static constexpr int G = Cfg<Q, M>::G;
+    int k;                        // index of the tile in the column: tile (J-k, J), t = k
+    WarpScratch<Q, M> *prod;      // scratch of the warp of column J-1 in this CTA, or null
+    bool consumer;                // the warp of column J+1 runs in this CTA and reads this warp's tiles
+    unsigned Wp[16];              // W[c'][c] of tile (J,J), packed pairs (set by tile 0)
+    int lB0[G], lC0[G];           // two-vector: features of middle block J-1 in column j (set by tile 1)
+    unsigned lcol0[16];           // plain: column j of tile (J-1,J), packed pairs (set by tile 1)
+    int colT;                     // D(IT, j) of the tile just finished: row 0 of the next tile's bottom neighbour
+    bool cnt_ok;                  // the next tile's chunk counter was complete when the last tile released
+    const int4 *tasks;            // tile tasks in diagonal order (chunk counts)
+};
+
+template <int Q, int M, bool COL>
 __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc &sd, int I, int J, int nfar,
-                                              WarpScratch<Q, M> &ws, const uint8_t *Rs, int lane, long long *tdeps) {
+                                              WarpScratch<Q, M> &ws, const uint8_t *Rs, int lane, long long *tdeps,
+                                              NearCol<Q, M> &cs) {
     using C = Cfg<Q, M>;
     constexpr int T = C::T, G = C::G;
     constexpr bool TV = (M == kTwoVector);
@@ -553,6 +622,25 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     const int NG = TV ? Np / Q : 1;
     const bool lateA = t >= 2;   // middle block K = J-1: rows of tile (I,J-1) x column of tile (J-1,J)
     const bool lateB = t >= 3;   // middle block K = I+1: rows of tile (I,I+1) x column of tile (I+1,J)
+    // column mode: tiles alternate between two buffers; the previous one holds tile (I+1,J)
+    const int buf = COL ? (cs.k & 1) : 0;
+    int16_t(*tile)[33] = buf ? ws.tile1 : ws.tile;
+    const int16_t(*ptile)[33] = buf ? ws.tile : ws.tile1;
+    WarpScratch<Q, M> *prod = COL ? cs.prod : nullptr;
+    const int pbp = (cs.k - 1) & 1;   // buffer of the producer's tile (I, J-1)
+    // column mode, chunk counter already seen complete: the partial maxima go out first
+    const bool early = COL && nfar > 0 && cs.cnt_ok;
+    int acc[T];
+    int *slot = P.pring + sd.p_off + ((size_t)(t % kRing) * NT + I) * (T * T);
+    if (early) {
+#pragma unroll
+        for (int r = 0; r < T; ++r) acc[r] = valid ? __ldcg(slot + r * T + c) : 0;
+    }
+    // codes of the tile's rows (one per lane) and of this lane's column, for the pair bits
+    const int rcode = lane < T ? (int)codes[IT + lane] : kPadCode;
+    const int sj = valid ? (int)codes[j] : kPadCode;
+    // column mode: chunk count of the column's next tile (I-1, J)
+    const int nn_next = (COL && I > 0) ? __ldg(&cs.tasks[(t + 1) * NT - (t + 1) * t / 2 + (I - 1)].z) : 0;
 
     // ---- inputs from tiles finished long before the neighbours, all loads in flight at once
     unsigned Wp[16];           // packed W[c'][c] = D(JT+c'+1, j) for c' < c, sentinel otherwise
@@ -565,30 +653,44 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll
         for (int v = 0; v < 16; ++v) lcol[k][v] = 0;
     }
-    if (valid) ws.rcode[c] = codes[IT + c];
-    // pair bits of this lane's column against the tile's 32 rows: bit r = b(S_{IT+r}, S_j)
-    const int sj = valid ? (int)codes[j] : kPadCode;
-    unsigned pbits = 0;
-#pragma unroll
-    for (int r = 0; r < T; ++r) {
-        const int si = (int)codes[IT + r];
-        pbits |= (unsigned)((P.pair64 >> (8 * si + sj)) & 1ull) << r;
+    if constexpr (COL) {
+        // the next column's warp must have read the tile two back before its buffer is rewritten
+        if (cs.consumer && cs.k >= 2 && !wait_smem_geq(&ws.consumed, cs.k - 1, P.error, P.timeout_ns, lane)) return 0;
+        // left neighbour (I, J-1), from the warp of column J-1 in this CTA or else through its flag; it
+        // implies every tile of row I to its left, (I,I) and (I,I+1) among them.  The bottom neighbour
+        // (I+1, J) is this warp's previous tile.  A complete chunk counter (seen before the last
+        // release) implies them too: the chunk of middle block I+2 waited for tile (I, I+2).  Then the
+        // loads of old tiles go out first and the left neighbour is awaited after them.
+        if (t >= 1 && !early) {
+            if (prod) {
+                if (!wait_smem_geq(&prod->produced, cs.k, P.error, P.timeout_ns, lane)) return 0;
+            } else if (!warp_wait_geq(flags + I * NT + (J - 1), 1, P, lane)) {
+                return 0;
+            }
+        }
     }
     if (t >= 1) {
-        if (!warp_wait_geq(flags + I * NT + I, 1, P, lane)) return 0;
-        if (!warp_wait_geq(flags + J * NT + J, 1, P, lane)) return 0;
-        if (lateA && !warp_wait_geq(flags + (J - 1) * NT + J, 1, P, lane)) return 0;
-        if (lateB && !warp_wait_geq(flags + I * NT + (I + 1), 1, P, lane)) return 0;
+        if constexpr (!COL) {
+            if (!warp_wait_geq(flags + I * NT + I, 1, P, lane)) return 0;
+            if (!warp_wait_geq(flags + J * NT + J, 1, P, lane)) return 0;
+            if (lateA && !warp_wait_geq(flags + (J - 1) * NT + J, 1, P, lane)) return 0;
+            if (lateB && !warp_wait_geq(flags + I * NT + (I + 1), 1, P, lane)) return 0;
+        }
         int16_t dv[T];
 #pragma unroll
         for (int r = 0; r < T; ++r) dv[r] = valid ? __ldcg(Drow + (size_t)(IT + r) * Np + IT + c) : (int16_t)0;
+        if constexpr (COL) {
 #pragma unroll
-        for (int mm = 0; mm < 16; ++mm) {
-            const int c0 = 2 * mm, c1 = 2 * mm + 1;
-            int w0 = kNeg16, w1 = kNeg16;
-            if (valid && c0 < c) w0 = ldcg16(Dcol + (size_t)j * PC + JT + c0 + 1 + kColOff);
-            if (valid && c1 < c) w1 = ldcg16(Dcol + (size_t)j * PC + JT + c1 + 1 + kColOff);
-            Wp[mm] = (unsigned)(w0 & 0xffff) | ((unsigned)w1 << 16);
+            for (int mm = 0; mm < 16; ++mm) Wp[mm] = cs.Wp[mm];
+        } else {
+#pragma unroll
+            for (int mm = 0; mm < 16; ++mm) {
+                const int c0 = 2 * mm, c1 = 2 * mm + 1;
+                int w0 = kNeg16, w1 = kNeg16;
+                if (valid && c0 < c) w0 = ldcg16(Dcol + (size_t)j * PC + JT + c0 + 1 + kColOff);
+                if (valid && c1 < c) w1 = ldcg16(Dcol + (size_t)j * PC + JT + c1 + 1 + kColOff);
+                Wp[mm] = (unsigned)(w0 & 0xffff) | ((unsigned)w1 << 16);
+            }
         }
         if constexpr (TV) {
             constexpr int E = (T * G + 31) / 32;   // row features of (I,I) and (I,I+1), spread over the warp
@@ -604,9 +706,14 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             if (lateA && valid) {
 #pragma unroll
                 for (int gl = 0; gl < G; ++gl) {
-                    const uint32_t cf = __ldcg(CF + (size_t)((J - 1) * G + gl) * Np + j);
-                    lB[0][gl] = (int)(cf >> 16);
-                    lC[0][gl] = (int)(cf & C::BMASK);
+                    if constexpr (COL) {
+                        lB[0][gl] = cs.lB0[gl];
+                        lC[0][gl] = cs.lC0[gl];
+                    } else {
+                        const uint32_t cf = __ldcg(CF + (size_t)((J - 1) * G + gl) * Np + j);
+                        lB[0][gl] = (int)(cf >> 16);
+                        lC[0][gl] = (int)(cf & C::BMASK);
+                    }
                 }
             }
 #pragma unroll
@@ -625,11 +732,16 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
                 for (int v = 0; v < 4; ++v) dst[v] = __ldcg(src + v);
             }
             if (lateA) {   // column j of tile (J-1, J): rows (J-1)T+1 .. JT
-                const uint4 *cs = reinterpret_cast<const uint4 *>(Dcol + (size_t)j * PC + (J - 1) * T + 1 + kColOff);
+                if constexpr (COL) {
 #pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    uint4 w = __ldcg(cs + v);
-                    lcol[0][4 * v] = w.x; lcol[0][4 * v + 1] = w.y; lcol[0][4 * v + 2] = w.z; lcol[0][4 * v + 3] = w.w;
+                    for (int v = 0; v < 16; ++v) lcol[0][v] = cs.lcol0[v];
+                } else {
+                    const uint4 *cp = reinterpret_cast<const uint4 *>(Dcol + (size_t)j * PC + (J - 1) * T + 1 + kColOff);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        uint4 w = __ldcg(cp + v);
+                        lcol[0][4 * v] = w.x; lcol[0][4 * v + 1] = w.y; lcol[0][4 * v + 2] = w.z; lcol[0][4 * v + 3] = w.w;
+                    }
                 }
             }
         }
@@ -642,18 +754,40 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     }
 
     // ---- the two neighbours that finish last
-    if (t >= 1) {
-        if (!warp_wait_geq(flags + I * NT + (J - 1), 1, P, lane)) return 0;
-        if (!warp_wait_geq(flags + (I + 1) * NT + J, 1, P, lane)) return 0;
+    if constexpr (!COL) {
+        if (t >= 1) {
+            if (!warp_wait_geq(flags + I * NT + (J - 1), 1, P, lane)) return 0;
+            if (!warp_wait_geq(flags + (I + 1) * NT + J, 1, P, lane)) return 0;
+        }
+    } else {
+        if (t >= 1 && early) {
+            if (prod) {
+                if (!wait_smem_geq(&prod->produced, cs.k, P.error, P.timeout_ns, lane)) return 0;
+            } else if (!warp_wait_geq(flags + I * NT + (J - 1), 1, P, lane)) {
+                return 0;
+            }
+        }
     }
     if (P.trace) tdeps[0] = (long long)gtimer();
     // every load that depends on the neighbours goes out at once
     int colT = 0;              // D((I+1)T, j): row 0 of tile (I+1, J)
     int leftv = 0;             // D(IT+1+c, JT-1): left column for lane 0's pair term
     if (t >= 1 && valid) {
-        if ((I + 1) * T < Np) colT = ldcg16(Drow + (size_t)((I + 1) * T) * Np + j);
         const int row = IT + 1 + c;
-        if (row <= JT - 1 && row < Np) leftv = ldcg16(Dcol + (size_t)(JT - 1) * PC + row + kColOff);
+        if constexpr (COL) {
+            colT = cs.colT;
+            if (prod) {
+                // the producer's tile has row T = D((I+1)T, JT-1), which is 0 when t = 1
+                const int16_t(*pt)[33] = pbp ? prod->tile1 : prod->tile;
+                leftv = (int)pt[c + 1][T - 1];
+            } else if (row <= JT - 1 && row < Np) {
+                // two-vector column mode keeps no column-major copy
+                leftv = TV ? ldcg16(Drow + (size_t)row * Np + (JT - 1)) : ldcg16(Dcol + (size_t)(JT - 1) * PC + row + kColOff);
+            }
+        } else {
+            if ((I + 1) * T < Np) colT = ldcg16(Drow + (size_t)((I + 1) * T) * Np + j);
+            if (row <= JT - 1 && row < Np) leftv = ldcg16(Dcol + (size_t)(JT - 1) * PC + row + kColOff);
+        }
     }
     constexpr int E = (T * G + 31) / 32;
     uint32_t fa[E];            // row features of tile (I, J-1) (two-vector, late block K = J-1)
@@ -662,37 +796,65 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int idx = e * 32 + lane;
-            fa[e] = (lateA && idx < T * G) ? __ldcg(RF + (size_t)(IT + idx / G) * NG + (J - 1) * G + idx % G) : 0u;
+            const bool in = lateA && idx < T * G;
+            if (COL && prod) fa[e] = in ? prod->rfo[pbp][idx / G][idx % G] : 0u;
+            else fa[e] = in ? __ldcg(RF + (size_t)(IT + idx / G) * NG + (J - 1) * G + idx % G) : 0u;
         }
         if (lateB && valid) {
 #pragma unroll
             for (int gl = 0; gl < G; ++gl) {
-                const uint32_t cf = __ldcg(CF + (size_t)((I + 1) * G + gl) * Np + j);
+                // column mode: the features of block I+1 are this warp's previous tile's
+                const uint32_t cf = COL ? ws.cbc[gl][c] : __ldcg(CF + (size_t)((I + 1) * G + gl) * Np + j);
                 lB[1][gl] = (int)(cf >> 16);
                 lC[1][gl] = (int)(cf & C::BMASK);
             }
         }
     } else {
-        const uint4 *src = reinterpret_cast<const uint4 *>(Drow + (size_t)(IT + lane) * Np + (J - 1) * T);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) ra[v] = lateA ? __ldcg(src + v) : make_uint4(0u, 0u, 0u, 0u);
-        if (lateB) {   // column j of tile (I+1, J): rows (I+1)T+1 .. (I+2)T
-            const uint4 *cs = reinterpret_cast<const uint4 *>(Dcol + (size_t)j * PC + (I + 1) * T + 1 + kColOff);
+        if (COL && prod) {
+            const int16_t(*pt)[33] = pbp ? prod->tile1 : prod->tile;
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                uint4 w = __ldcg(cs + v);
-                lcol[1][4 * v] = w.x; lcol[1][4 * v + 1] = w.y; lcol[1][4 * v + 2] = w.z; lcol[1][4 * v + 3] = w.w;
+                unsigned w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    w[e] = lateA ? ((unsigned)(uint16_t)pt[lane][8 * v + 2 * e] | ((unsigned)(uint16_t)pt[lane][8 * v + 2 * e + 1] << 16)) : 0u;
+                ra[v] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        } else {
+            const uint4 *src = reinterpret_cast<const uint4 *>(Drow + (size_t)(IT + lane) * Np + (J - 1) * T);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) ra[v] = lateA ? __ldcg(src + v) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        if (lateB) {   // column j of tile (I+1, J): rows (I+1)T+1 .. (I+2)T
+            if constexpr (COL) {
+#pragma unroll
+                for (int w = 0; w < 16; ++w)
+                    lcol[1][w] = (unsigned)(uint16_t)ptile[1 + 2 * w][c] | ((unsigned)(uint16_t)ptile[2 + 2 * w][c] << 16);
+            } else {
+                const uint4 *cp = reinterpret_cast<const uint4 *>(Dcol + (size_t)j * PC + (I + 1) * T + 1 + kColOff);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    uint4 w = __ldcg(cp + v);
+                    lcol[1][4 * v] = w.x; lcol[1][4 * v + 1] = w.y; lcol[1][4 * v + 2] = w.z; lcol[1][4 * v + 3] = w.w;
+                }
             }
         }
     }
+    if constexpr (COL) {
+        // everything of the producer's tile has been read: its buffer may be reused
+        if (prod && t >= 1) {
+            __syncwarp();
+            if (lane == 0) st_release_cta(&prod->consumed, cs.k);
+        }
+    }
     // partial max of the FAR chunks (middle blocks I+2 .. J-2)
-    int acc[T];
-    int *slot = P.pring + sd.p_off + ((size_t)(t % kRing) * NT + I) * (T * T);
     if (nfar > 0) {
-        if (!warp_wait_geq(P.cnt + sd.cnt_off + I * NT + J, nfar, P, lane)) return 0;
-        if (P.trace) tdeps[1] = (long long)gtimer();
+        if (!early) {
+            if (!warp_wait_geq(P.cnt + sd.cnt_off + I * NT + J, nfar, P, lane)) return 0;
 #pragma unroll
-        for (int r = 0; r < T; ++r) acc[r] = valid ? __ldcg(slot + r * T + c) : 0;
+            for (int r = 0; r < T; ++r) acc[r] = valid ? __ldcg(slot + r * T + c) : 0;
+        }
+        if (P.trace) tdeps[1] = (long long)gtimer();
     } else {
 #pragma unroll
         for (int r = 0; r < T; ++r) acc[r] = 0;
@@ -715,12 +877,23 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         for (int kb = 0; kb < 2; ++kb) {
             if (kb == 0 ? lateA : lateB) {
 #pragma unroll
-                for (int gl = 0; gl < G; ++gl) {
+                for (int r = 0; r < T; ++r) {
+                    uint32_t fr[G];   // the row's features, one 16-byte load per four groups
+                    if constexpr (G % 4 == 0) {
+                        const uint4 *pv = reinterpret_cast<const uint4 *>(&ws.lrf[kb][r][0]);
 #pragma unroll
-                    for (int r = 0; r < T; ++r) {
-                        const uint32_t f = ws.lrf[kb][r][gl];
-                        const int v = rlookup<Q>(Rs, hrow_offset<Q>((int)(f & C::BMASK)), lC[kb][gl]);
-                        acc[r] = max(acc[r], (int)(f >> 16) + lB[kb][gl] + v);
+                        for (int v4 = 0; v4 < G / 4; ++v4) {
+                            const uint4 w = pv[v4];
+                            fr[4 * v4] = w.x; fr[4 * v4 + 1] = w.y; fr[4 * v4 + 2] = w.z; fr[4 * v4 + 3] = w.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int gl = 0; gl < G; ++gl) fr[gl] = ws.lrf[kb][r][gl];
+                    }
+#pragma unroll
+                    for (int gl = 0; gl < G; ++gl) {
+                        const int v = rlookup<Q>(Rs, hrow_offset<Q>((int)(fr[gl] & C::BMASK)), lC[kb][gl]);
+                        acc[r] = max(acc[r], (int)(fr[gl] >> 16) + lB[kb][gl] + v);
                     }
                 }
             }
@@ -758,7 +931,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 
     if (valid) {
         ws.left[c + 1] = (int16_t)leftv;
-        ws.tile[T][c] = (int16_t)colT;
+        tile[T][c] = (int16_t)colT;
     }
     if (c == 0) ws.left[0] = 0;
     if constexpr (!TV) {
@@ -825,7 +998,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     // publishes row r (value d of this lane's column): tile copy, row-major store, vertical and
     // horizontal difference vectors
     auto publish = [&](int r, int d, int below_prev) {
-        ws.tile[r][c] = (int16_t)d;
+        tile[r][c] = (int16_t)d;
         if (T == 32 || valid) Drow[(size_t)(IT + r) * Np + j] = (int16_t)d;
         const int vb = d - below_prev;   // vertical difference D(i,j) - D(i+1,j)
         vhist = (vhist << 1) | (unsigned)(vb & 1);
@@ -845,6 +1018,15 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         }
     };
 
+    // pair bits of this lane's column against the tile's rows, bit r = b(S_{IT+r}, S_j): one ballot
+    // per base the column may hold (padding codes pair with nothing)
+    unsigned pbits;
+    {
+        unsigned pbx[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) pbx[x] = __ballot_sync(FULL, (P.pair64 >> (8 * rcode + x)) & 1ull);
+        pbits = sj == 0 ? pbx[0] : sj == 1 ? pbx[1] : sj == 2 ? pbx[2] : sj == 3 ? pbx[3] : 0u;
+    }
     int below = colT;          // D(i+1, j)
     if (t == 0) {
         // diagonal tile: every split lies in this tile, so the closure alone covers them; W is this
@@ -869,7 +1051,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
                 for (int e = 0; e < 4; ++e) {
                     const int c0 = 8 * v + 2 * e, c1 = c0 + 1;
                     const int r0 = (c0 + 1 <= T) ? c0 + 1 : T, r1 = (c1 + 1 <= T) ? c1 + 1 : T;
-                    const int t0 = (int)ws.tile[r0][c], t1 = (int)ws.tile[r1][c];
+                    const int t0 = (int)tile[r0][c], t1 = (int)tile[r1][c];
                     const int w0 = (c0 < c && c0 >= r && c0 + 1 <= T) ? t0 : kNeg16;
                     const int w1 = (c1 < c && c1 >= r && c1 + 1 <= T) ? t1 : kNeg16;
                     wp[e] = (unsigned)(w0 & 0xffff) | ((unsigned)w1 << 16);
@@ -934,6 +1116,12 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     }
     __syncwarp();
     if (P.trace) tdeps[2] = (long long)gtimer();
+    // column mode: the next tile's chunk counter, read now and acquired by the fence that releases
+    // this tile
+    int cnt_next = 0;
+    if constexpr (COL) {
+        if (lane == 0 && nn_next > 0) cnt_next = ld_relaxed(P.cnt + sd.cnt_off + (I - 1) * NT + J);
+    }
     if constexpr (TV) {
         // horizontal difference vectors of the finished rows, packed with one ballot per row (bit c =
         // D(i,JT+c) - D(i,JT+c-1)); the rows are independent, so their shuffle/ballot chains overlap
@@ -942,34 +1130,88 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         int av[T];
 #pragma unroll
         for (int r = 0; r < T; ++r) {
-            const int d = (int)ws.tile[r][c];
-            const int dl = (int)ws.tile[r][c > 0 ? c - 1 : 0];
+            const int d = (int)tile[r][c];
+            const int dl = (int)tile[r][c > 0 ? c - 1 : 0];
             up[r] = (d - dl) == 1;
-            av[r] = (int)ws.tile[r][(c < G) ? c * Q : 0];
+            av[r] = (int)tile[r][(c < G) ? c * Q : 0];
         }
         unsigned hb[T];
 #pragma unroll
         for (int r = 0; r < T; ++r) hb[r] = __ballot_sync(FULL, up[r]);
         if (c < G) {
 #pragma unroll
-            for (int r = 0; r < T; ++r)
-                P.rf[sd.rf_off + (size_t)(IT + r) * NG + J * G + c] = ((uint32_t)av[r] << 16) | ((hb[r] >> (c * Q + 1)) & C::BMASK);
+            for (int r = 0; r < T; ++r) {
+                const uint32_t f = ((uint32_t)av[r] << 16) | ((hb[r] >> (c * Q + 1)) & C::BMASK);
+                P.rf[sd.rf_off + (size_t)(IT + r) * NG + J * G + c] = f;
+                if constexpr (COL) {
+                    if (cs.consumer) ws.rfo[buf][r][c] = f;
+                }
+            }
         }
     }
-    // ---- column-major copy (lane = row)
-    if (lane < T) {
+    if constexpr (COL) {
+        // the tile (and its row features) is complete in shared memory: hand it to the next column's
+        // warp before the slower global copies and the release below
+        if (cs.consumer) {
+            __syncwarp();
+            if (lane == 0) st_release_cta(&ws.produced, cs.k + 1);
+        }
+    }
+    // ---- column-major copy (lane = row); two-vector column mode reads columns only as features
+    if (lane < T && !(COL && TV)) {
 #pragma unroll 8
-        for (int cc = 0; cc < T; ++cc) Dcol[(size_t)(JT + cc) * PC + IT + lane + kColOff] = ws.tile[lane][cc];
+        for (int cc = 0; cc < T; ++cc) Dcol[(size_t)(JT + cc) * PC + IT + lane + kColOff] = tile[lane][cc];
     }
     // answer D(0, n-1)
     if (I == 0 && J == NT - 1) {
         const int cn = (sd.n - 1) - JT;
-        if (sd.n >= 1 && lane == cn) P.results[sd.result_index] = (sd.n >= 2) ? (int)ws.tile[0][cn] : 0;
+        if (sd.n >= 1 && lane == cn) P.results[sd.result_index] = (sd.n >= 2) ? (int)tile[0][cn] : 0;
+    }
+    if constexpr (COL) {
+        // carry the column's constants and the bottom row to the next tile of this column
+        if (cs.k == 0) {
+#pragma unroll
+            for (int mm = 0; mm < 16; ++mm) {
+                const int c0 = 2 * mm, c1 = 2 * mm + 1;
+                const int w0 = (valid && c0 < c) ? (int)tile[min(c0 + 1, T)][c] : kNeg16;
+                const int w1 = (valid && c1 < c) ? (int)tile[min(c1 + 1, T)][c] : kNeg16;
+                cs.Wp[mm] = (unsigned)(w0 & 0xffff) | ((unsigned)w1 << 16);
+            }
+        }
+        if (cs.k == 1) {
+            if constexpr (TV) {
+#pragma unroll
+                for (int gl = 0; gl < G; ++gl) {
+                    const uint32_t cf = ws.cbc[gl][c];
+                    cs.lB0[gl] = (int)(cf >> 16);
+                    cs.lC0[gl] = (int)(cf & C::BMASK);
+                }
+            } else {
+#pragma unroll
+                for (int w = 0; w < 16; ++w)
+                    cs.lcol0[w] = (unsigned)(uint16_t)tile[1 + 2 * w][c] | ((unsigned)(uint16_t)tile[2 + 2 * w][c] << 16);
+            }
+        }
+        cs.colT = below;
     }
     if (P.trace) tdeps[3] = (long long)gtimer();
-    __threadfence();
+    // every lane's stores are ordered before lane 0's release by the warp barrier; the release is
+    // cumulative, so a reader that acquires the flag sees the whole tile
     __syncwarp();
-    if (lane == 0) st_release(flags + I * NT + J, 1);
+    if constexpr (COL) {
+        // one fence serves as this tile's release and as the acquire of the next tile's chunk
+        // counter, read just before it
+        int seen = 0;
+        if (lane == 0) {
+            fence_acq_rel();
+            st_relaxed(flags + I * NT + J, 1);
+            seen = (nn_next > 0 && cnt_next >= nn_next) ? 1 : 0;
+        }
+        cs.cnt_ok = __shfl_sync(FULL, seen, 0) != 0;
+        __syncwarp();
+    } else {
+        if (lane == 0) st_release(flags + I * NT + J, 1);
+    }
     return tfar;
 }
 
@@ -986,11 +1228,52 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
         // the device copy of R is padded to a multiple of 256 bytes, so rounding up stays in bounds
         for (int v = threadIdx.x; v < (C::RBYTES + 15) / 16; v += blockDim.x) dst[v] = __ldg(src + v);
     }
+    WarpScratch<Q, M> *wsb = reinterpret_cast<WarpScratch<Q, M> *>(smem + round_up(C::RBYTES, 128));
+    WarpScratch<Q, M> &ws = wsb[warp];
+    if (lane == 0) {
+        ws.produced = 0;
+        ws.consumed = 0;
+    }
     __syncthreads();
-    WarpScratch<Q, M> &ws =
-        *reinterpret_cast<WarpScratch<Q, M> *>(smem + round_up(C::RBYTES, 128) + warp * sizeof(WarpScratch<Q, M>));
     const bool split = P.near_ctas > 0;
     const bool far_role = split && (int)blockIdx.x >= P.near_ctas;
+    if (P.col_mode && split && !far_role) {
+        // column mode: this warp computes the tiles of one column, bottom-up
+        const SeqDesc sd = P.seqs[0];
+        const int NT = sd.NT;
+        const int J = (int)blockIdx.x * P.cols_per_cta + warp;
+        if (warp >= P.cols_per_cta || J >= NT) return;
+        NearCol<Q, M> cs;
+        cs.prod = warp > 0 ? &wsb[warp - 1] : nullptr;
+        cs.consumer = (warp + 1 < P.cols_per_cta) && (J + 1 < NT);
+        cs.colT = 0;
+        cs.cnt_ok = false;
+        cs.tasks = P.tasks;
+        for (int k = 0; k <= J; ++k) {
+            const int I = J - k;
+            cs.k = k;
+            const int idx = k * NT - k * (k - 1) / 2 + I;   // tile (I,J) in the diagonal-ordered tile tasks
+            const int4 tk = P.tasks[idx];
+            long long t0 = 0, tdeps[4] = {0, 0, 0, 0};
+            if (P.trace && lane == 0) t0 = (long long)gtimer();
+            const long long tmid = run_near<Q, M, true>(P, sd, I, J, tk.z, ws, Rs, lane, tdeps, cs);
+            if (P.trace && lane == 0) {
+                long long *rec = P.trace + (size_t)idx * kTraceWords;
+                rec[0] = ((long long)(blockIdx.x * kWarpsPerCta + warp) << 32) | (unsigned)idx;
+                rec[1] = ((long long)kTaskNear << 32) | (unsigned)tk.x;
+                rec[2] = ((long long)I << 32) | (unsigned)J;
+                rec[3] = t0;
+                rec[4] = tdeps[0];
+                rec[5] = tmid;
+                rec[6] = (long long)gtimer();
+                rec[7] = tdeps[1];
+                rec[8] = tdeps[2];
+                rec[9] = tdeps[3];
+            }
+            if (*(volatile int *)P.error != 0) break;
+        }
+        return;
+    }
     int *qhead = far_role ? P.queue_head_far : P.queue_head;
     const int qbase = far_role ? P.nnear : 0;
     const int qlimit = (split && !far_role) ? P.nnear : P.ntasks;
@@ -1007,7 +1290,14 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
         if (P.trace && lane == 0) t0 = (long long)gtimer();
         long long tmid;
         const int ty = task_type(tk.y);
-        if (ty == kTaskNear) tmid = run_near<Q, M>(P, sd, I, J, tk.z, ws, Rs, lane, tdeps);
+        if (ty == kTaskNear) {
+            NearCol<Q, M> none;
+            none.k = 0;
+            none.prod = nullptr;
+            none.consumer = false;
+            none.cnt_ok = false;
+            tmid = run_near<Q, M, false>(P, sd, I, J, tk.z, ws, Rs, lane, tdeps, none);
+        }
         else if (ty == kTaskFar) tmid = run_far<Q, M>(P, sd, I, J, tk.z, tk.w, ws, Rs, lane, tdeps);
         else tmid = run_far_strip<Q, M>(P, sd, I, J, tk.z, tk.w, ws, Rs, lane, tdeps);
         if (P.trace && lane == 0) {

@@ -12,8 +12,9 @@
     - Eq. 1 re-evaluated from the returned table at sampled cells, including
       the answer cell (0, n-1);
     - the plain kernel's table equals the two-vector kernel's.
-* The split task queues (tile-only CTAs) forced on at sizes the oracle
-  finishes quickly, so that path is compared element by element too.
+* The split task queues (tile-only CTAs), with and without column mode,
+  forced on at sizes the oracle finishes quickly, so those paths are
+  compared element by element too.
 """
 import numpy as np
 import pytest
@@ -85,17 +86,43 @@ def _large_checks(f, seq, mask, rng, D_other=None):
     return D
 
 
+# (n, tile CTAs, column mode): 700 bases are 22 tile columns, 2000 bases 63 (q = 8), so one tile
+# CTA (8 warps) cannot hold every column and three can; column mode off keeps the tile-task queue
+SPLITS = [(700, 1, -1), (700, 3, 0), (700, 3, -1), (2000, 8, 0), (2000, 8, -1), (2000, 30, -1), (1500, 6, 8), (1500, 12, 4), (2000, 33, 2)]
+
+
 @pytest.mark.parametrize("method", ["two_vector", "plain"])
-@pytest.mark.parametrize("n,near", [(700, 1), (700, 3), (2000, 8), (2000, 30)])
-def test_split_queues_full_table(method, n, near):
+@pytest.mark.parametrize("n,near,cols", SPLITS)
+def test_split_queues_full_table(method, n, near, cols):
     f = fold.Folder(q=8, method=method)
     try:
         f.option(fold.FOLD_OPT_NEAR_CTAS, near)
+        f.option(fold.FOLD_OPT_COLUMNS, cols)
         seq = synth.uniform(n, 4242 + n + near)
         mp, D = f.score(seq, want_D=True)
         ref = oracle.nussinov(seq)
         assert mp == int(ref[0, n - 1])
         _full_equal(D, ref)
+    finally:
+        f.close()
+
+
+@pytest.mark.parametrize("q", [2, 3, 4, 6, 10])
+def test_column_mode_all_q(q):
+    """Column mode with every tile width (T = 30 for q = 3, 6, 10) and group count."""
+    f = fold.Folder(q=q)
+    try:
+        n = 37 * f.tile + 11   # 38 tile columns
+        f.option(fold.FOLD_OPT_NEAR_CTAS, (37 + 1 + 7) // 8)
+        for kind in ["uniform", "structured"]:
+            seq = synth.variant(kind, n, 500 + q)
+            ref = oracle.nussinov(seq)
+            # 8 columns per CTA (shared-memory handoffs) and 1 (every left neighbour through its flag)
+            for cpc in [8, 1]:
+                f.option(fold.FOLD_OPT_COLUMNS, cpc)
+                mp, D = f.score(seq, want_D=True)
+                assert mp == int(ref[0, n - 1])
+                _full_equal(D, ref)
     finally:
         f.close()
 
