@@ -104,7 +104,7 @@ static __device__ __forceinline__ void st_release_cta(int *p, int v) {
 }
 // Lane 0 waits (bounded) until the shared word *p >= target; the error word and the clock are
 // checked every 32 polls so that a poll costs one shared load.
-static __device__ __noinline__ bool wait_smem_geq(const int *p, int target, int *error, long long timeout_ns, int lane) {
+static __device__ __noinline__ bool wait_smem_geq_slow(const int *p, int target, int *error, long long timeout_ns, int lane) {
     int ok = 1;
     if (lane == 0 && ld_acquire_cta(p) < target) {
         const unsigned long long t0 = gtimer();
@@ -123,6 +123,15 @@ static __device__ __noinline__ bool wait_smem_geq(const int *p, int target, int 
     ok = __shfl_sync(FULL, ok, 0);
     __syncwarp();
     return ok != 0;
+}
+static __device__ __forceinline__ bool wait_smem_geq(const int *p, int target, int *error, long long timeout_ns, int lane) {
+    int v = 0;
+    if (lane == 0) v = ld_acquire_cta(p);
+    if (__shfl_sync(FULL, v, 0) >= target) {
+        __syncwarp();
+        return true;
+    }
+    return wait_smem_geq_slow(p, target, error, timeout_ns, lane);
 }
 
 static __device__ __forceinline__ int lds16(const int16_t *p) { return (int)*p; }
@@ -147,6 +156,7 @@ struct __align__(16) WarpScratch {
     static constexpr int LR = PL ? 32 : 1;         // plain: late-block row strips
     static constexpr int LF = PL ? 1 : T;          // two-vector: late-block row features
     static constexpr int SS = strip_of(Q, M);
+    static constexpr int DS = PL ? 40 : 32;    // diagonal-tile row stride: 16-byte rows (uint4 / cp.async)
     union {
         struct {                       // chunk tasks
             int2 rf[G][32];            // FAR staging (two-vector): (A, h-row byte offset)
@@ -165,9 +175,8 @@ struct __align__(16) WarpScratch {
     alignas(16) uint32_t lrf[2][LF][G];  // NEAR late blocks (two-vector): row features of (I,J-1), (I,I+1)
     uint32_t cbc[G + 1][32];           // NEAR (two-vector): (base << 16 | bits) of the lane's column groups;
                                        // row G takes the stores of rows that complete no group
-    static constexpr int DS = PL ? 40 : T + 2;   // row stride (plain reads rows as uint4)
     alignas(16) int16_t diag[T][DS];   // diagonal tile (I,I) rows
-    uint32_t drf[T][G];                // diagonal tile row features
+    alignas(16) uint32_t drf[T][G];    // diagonal tile row features
     int16_t pm[T][32];                 // far partial max of each row (lane = column)
     alignas(16) int16_t y[2][32];      // closure exchange, double-buffered (read back as uint4)
     int16_t left[T + 2];               // D(IT+m, JT-1)
@@ -185,7 +194,7 @@ struct ScratchChecks {
     static_assert(offsetof(WS, rows) % 16 == 0, "rows must be 16-byte aligned");
     static_assert(offsetof(WS, lrow) % 16 == 0, "lrow must be 16-byte aligned");
     static_assert(offsetof(WS, lrf) % 16 == 0, "lrf must be 16-byte aligned");
-    static_assert(M != kPlain || (offsetof(WS, diag) % 16 == 0 && (WS::DS * 2) % 16 == 0), "diag rows 16-byte aligned");
+    static_assert(offsetof(WS, diag) % 16 == 0 && (WS::DS * 2) % 16 == 0, "diag rows 16-byte aligned");
     static_assert(sizeof(WarpScratch<Q, M>) % 16 == 0, "scratch stride must keep 16-byte alignment");
     static constexpr bool ok = true;
 };
@@ -598,6 +607,7 @@ struct NearCol {
     int colT;                     // D(IT, j) of the tile just finished: row 0 of the next tile's bottom neighbour
     bool cnt_ok;                  // the next tile's chunk counter was complete when the last tile released
     const int4 *tasks;            // tile tasks in diagonal order (chunk counts)
+    bool failed;                  // the last tile stopped on a failed wait
 };
 
 template <int Q, int M, bool COL>
@@ -628,14 +638,17 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     const int16_t(*ptile)[33] = buf ? ws.tile : ws.tile1;
     WarpScratch<Q, M> *prod = COL ? cs.prod : nullptr;
     const int pbp = (cs.k - 1) & 1;   // buffer of the producer's tile (I, J-1)
-    // column mode, chunk counter already seen complete: the partial maxima go out first
+    // old-tile inputs: diagonal tile rows and features, late block K = I+1 rows
+    auto &dg = ws.diag;
+    auto &drf = ws.drf;
+    auto &lrf1 = ws.lrf[1];
+    auto &lrow1 = ws.lrow[1];
+    if constexpr (COL) cs.failed = true;   // cleared when the tile completes
+    // column mode, chunk counter already seen complete: no wait, and the loads of old tiles go out
+    // before the left neighbour is awaited
     const bool early = COL && nfar > 0 && cs.cnt_ok;
     int acc[T];
     int *slot = P.pring + sd.p_off + ((size_t)(t % kRing) * NT + I) * (T * T);
-    if (early) {
-#pragma unroll
-        for (int r = 0; r < T; ++r) acc[r] = valid ? __ldcg(slot + r * T + c) : 0;
-    }
     // codes of the tile's rows (one per lane) and of this lane's column, for the pair bits
     const int rcode = lane < T ? (int)codes[IT + lane] : kPadCode;
     const int sj = valid ? (int)codes[j] : kPadCode;
@@ -678,7 +691,8 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         }
         int16_t dv[T];
 #pragma unroll
-        for (int r = 0; r < T; ++r) dv[r] = valid ? __ldcg(Drow + (size_t)(IT + r) * Np + IT + c) : (int16_t)0;
+        for (int r = 0; r < T; ++r)
+            dv[r] = valid ? __ldcg(Drow + (size_t)(IT + r) * Np + IT + c) : (int16_t)0;
         if constexpr (COL) {
 #pragma unroll
             for (int mm = 0; mm < 16; ++mm) Wp[mm] = cs.Wp[mm];
@@ -720,14 +734,14 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             for (int e = 0; e < E; ++e) {
                 const int idx = e * 32 + lane;
                 if (idx < T * G) {
-                    ws.drf[idx / G][idx % G] = fv[e];
-                    ws.lrf[1][idx / G][idx % G] = fb[e];
+                    drf[idx / G][idx % G] = fv[e];
+                    lrf1[idx / G][idx % G] = fb[e];
                 }
             }
         } else {
             if (lateB) {   // row strip of tile (I, I+1), row IT+lane
                 const uint4 *src = reinterpret_cast<const uint4 *>(Drow + (size_t)(IT + lane) * Np + (I + 1) * T);
-                uint4 *dst = reinterpret_cast<uint4 *>(&ws.lrow[1][lane][0]);
+                uint4 *dst = reinterpret_cast<uint4 *>(&lrow1[lane][0]);
 #pragma unroll
                 for (int v = 0; v < 4; ++v) dst[v] = __ldcg(src + v);
             }
@@ -747,7 +761,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         }
 #pragma unroll
         for (int r = 0; r < T; ++r)
-            if (valid) ws.diag[r][c] = dv[r];
+            if (valid) dg[r][c] = dv[r];
     } else {
 #pragma unroll
         for (int mm = 0; mm < 16; ++mm) Wp[mm] = 0;
@@ -849,11 +863,9 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     }
     // partial max of the FAR chunks (middle blocks I+2 .. J-2)
     if (nfar > 0) {
-        if (!early) {
-            if (!warp_wait_geq(P.cnt + sd.cnt_off + I * NT + J, nfar, P, lane)) return 0;
+        if (!early && !warp_wait_geq(P.cnt + sd.cnt_off + I * NT + J, nfar, P, lane)) return 0;
 #pragma unroll
-            for (int r = 0; r < T; ++r) acc[r] = valid ? __ldcg(slot + r * T + c) : 0;
-        }
+        for (int r = 0; r < T; ++r) acc[r] = valid ? __ldcg(slot + r * T + c) : 0;
         if (P.trace) tdeps[1] = (long long)gtimer();
     } else {
 #pragma unroll
@@ -880,7 +892,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
                 for (int r = 0; r < T; ++r) {
                     uint32_t fr[G];   // the row's features, one 16-byte load per four groups
                     if constexpr (G % 4 == 0) {
-                        const uint4 *pv = reinterpret_cast<const uint4 *>(&ws.lrf[kb][r][0]);
+                        const uint4 *pv = reinterpret_cast<const uint4 *>(kb == 0 ? &ws.lrf[0][r][0] : &lrf1[r][0]);
 #pragma unroll
                         for (int v4 = 0; v4 < G / 4; ++v4) {
                             const uint4 w = pv[v4];
@@ -888,7 +900,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
                         }
                     } else {
 #pragma unroll
-                        for (int gl = 0; gl < G; ++gl) fr[gl] = ws.lrf[kb][r][gl];
+                        for (int gl = 0; gl < G; ++gl) fr[gl] = kb == 0 ? ws.lrf[0][r][gl] : lrf1[r][gl];
                     }
 #pragma unroll
                     for (int gl = 0; gl < G; ++gl) {
@@ -904,7 +916,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             if (kb == 0 ? lateA : lateB) {
 #pragma unroll
                 for (int r = 0; r < T; ++r) {
-                    const uint4 *rw = reinterpret_cast<const uint4 *>(&ws.lrow[kb][r][0]);
+                    const uint4 *rw = reinterpret_cast<const uint4 *>(kb == 0 ? &ws.lrow[0][r][0] : &lrow1[r][0]);
                     unsigned a0 = 0, a1 = 0;
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
@@ -965,13 +977,13 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             for (int e = 0; e < Q - 2; ++e) {
                 const int kk = rr + 2 + e;
                 const int ix = min(kk, T);
-                const int v = (int)ws.diag[rr][ix - 1] + win[e];
+                const int v = (int)dg[rr][ix - 1] + win[e];
                 cand[k++] = (kk <= ce) ? v : kNeg16;
             }
             // full groups of tile column I completed before row rr+1 (g*q > rr)
 #pragma unroll
             for (int gl = 0; gl < G; ++gl) {
-                const uint32_t f = ws.drf[rr][gl];
+                const uint32_t f = drf[rr][gl];
                 const uint32_t cb = ws.cbc[gl][c];
                 const int v = rlookup<Q>(Rs, hrow_offset<Q>((int)(f & C::BMASK)), (int)(cb & C::BMASK));
                 cand[k++] = (gl * Q > rr) ? (int)(f >> 16) + (int)(cb >> 16) + v : kNeg16;
@@ -980,7 +992,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         } else {
             // every split with D(k,j) in this tile column: rows not yet done hold the sentinel
             unsigned acc2[4] = {0u, 0u, 0u, 0u};
-            const uint4 *dw = reinterpret_cast<const uint4 *>(&ws.diag[rr][0]);
+            const uint4 *dw = reinterpret_cast<const uint4 *>(&dg[rr][0]);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 const uint4 a = dw[v];
@@ -1080,7 +1092,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             int y = max(max(yold, pb + bl), below);
             if constexpr (TV) {
                 const int gl = r / Q;   // < G for every r < T; completed by row r+1 when r % Q == 0
-                const uint32_t f = ws.drf[r][gl];
+                const uint32_t f = drf[r][gl];
                 const uint32_t cb = last_cb;
                 const int v = rlookup<Q>(Rs, hrow_offset<Q>((int)(f & C::BMASK)), (int)(cb & C::BMASK));
                 const int cand = (int)(f >> 16) + (int)(cb >> 16) + v;
@@ -1208,6 +1220,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             seen = (nn_next > 0 && cnt_next >= nn_next) ? 1 : 0;
         }
         cs.cnt_ok = __shfl_sync(FULL, seen, 0) != 0;
+        cs.failed = false;
         __syncwarp();
     } else {
         if (lane == 0) st_release(flags + I * NT + J, 1);
@@ -1270,7 +1283,7 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
                 rec[8] = tdeps[2];
                 rec[9] = tdeps[3];
             }
-            if (*(volatile int *)P.error != 0) break;
+            if (cs.failed) break;   // a wait gave up (its error is in P.error)
         }
         return;
     }
