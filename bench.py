@@ -18,8 +18,11 @@ host cores instead, on a bounded prefix of the same input per step.
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -34,6 +37,36 @@ sys.path.insert(0, ROOT)
 METRIC = "DP cells/s at n=6000 vs plain GPU Nussinov; batched seq/s; serve p50/p99 ms"
 UNIT = "cells/s"
 L2_FLUSH_BYTES = 256 << 20
+
+
+DRAM_PROFILE = os.path.join(ROOT, "profiles", "fold_kernel_n6000_dram.md")
+
+
+def kernel_source_hash() -> str:
+    """sha256 over the library's device and scheduling sources, in name order."""
+    h = hashlib.sha256()
+    for path in sorted(glob.glob(os.path.join(ROOT, "paper_1307_7820_b300", "csrc", "*"))):
+        if path.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(os.path.basename(path).encode())
+            with open(path, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(n: int, q: int):
+    """DRAM bytes per launch of the two-vector fold kernel from the committed ncu summary, or None
+    when that summary was taken on other sources (the kernel changed since) or another workload."""
+    try:
+        text = open(DRAM_PROFILE).read()
+    except OSError:
+        return None
+    got = dict(re.findall(r"^- (\w+): (\S+)$", text, re.M))
+    if got.get("source_sha256") != kernel_source_hash() or got.get("workload") != f"n{n}_q{q}":
+        return None
+    try:
+        return float(got["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def parse_args():
@@ -406,7 +439,8 @@ def main():
     achieved = lam / (kern_ms * 1e-3)
     roofline = {
         "bound": "alu", "unit": "Glookups/s", "achieved": achieved / 1e9, "peak": peak / 1e9,
-        "frac": achieved / peak, "traffic": None,
+        "frac": achieved / peak, "traffic": measured_traffic(n, q),
+        "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
         "kernel": "fold_kernel<8,two-vector> (persistent)", "kernel_ms": kern_ms,
         "algorithmic_lookups": lam,
         "peak_basis": f"{n_sm} SMs x 32 conflict-free shared-memory lookups/clk x 2032 MHz max SM clock",
