@@ -80,8 +80,9 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-qsweep", action="store_true")
     ap.add_argument("--trace", default="", help="write a per-task trace of one fold to this .npy file")
-    ap.add_argument("--serve-rates", default="200,1000",
+    ap.add_argument("--serve-rates", default="50,200,1000,2000",
                     help="Poisson arrival rates (req/s) for the serving run; the workload lists 50-2000")
     ap.add_argument("--serve-seconds", type=float, default=1.5, help="arrival window per rate")
     return ap.parse_args()
@@ -90,7 +91,8 @@ def parse_args():
 def workload_config(a):
     return {
         "workload": f"single RNA sequence n={a.n}, i.i.d. uniform ACGU (seed 1308), pair set AU,UA,CG,GC,GU,UG, "
-                    f"no minimum hairpin, two-vector q={a.q}, int16 D stored row- and column-major",
+                    f"no minimum hairpin, two-vector q={a.q}, int16 D (row-major; a column-major copy where a "
+                    f"kernel reads columns)",
         "n": a.n,
         "q": a.q,
         "pair_mask": "0x5A48",
@@ -166,6 +168,19 @@ def cpu_oracle_sample(seq: str, prefix: int):
     scale = (n / prefix) ** 3 if prefix < n else 1.0
     full_s = dt * scale
     return full_s, dt
+
+
+def cpu_two_vector_sample(seq: str, prefix: int, q: int):
+    """Time the oracle's CPU two-vector (Algorithm 1) on seq[:prefix]; project by n^3."""
+    import oracle
+    oracle.build()
+    s = seq[:prefix]
+    t0 = time.perf_counter()
+    oracle.two_vector(s, q)
+    dt = time.perf_counter() - t0
+    n = len(seq)
+    scale = (n / prefix) ** 3 if prefix < n else 1.0
+    return dt * scale, dt
 
 
 def run_reference(a):
@@ -424,14 +439,47 @@ def main():
         serve = serve_bench(tv, [float(x) for x in a.serve_rates.split(",") if x], a.serve_seconds, dev, stream,
                             torch, fold, metrics, synth)
 
-    # ---- CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
+    # ---- q sweep of the same fold (device time, best of 3 per q, automatic work split)
+    qsweep = None
+    if not a.no_qsweep:
+        qsweep = {}
+        for qq in range(4, 11):
+            fq = fold.Folder(q=qq, device=local)
+            codes = torch.from_numpy(fold.encode_codes(seq)).to(dev)
+            wsq = torch.empty(fq.workspace_bytes(n), dtype=torch.uint8, device=dev)
+            outq = torch.zeros(1, dtype=torch.int32, device=dev)
+            ts = []
+            for k in range(4):
+                with torch.cuda.stream(stream):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fq.score_dev(codes, wsq, outq, None, stream=stream.cuda_stream)
+                    e1.record(stream)
+                e1.synchronize()
+                if k > 0:
+                    ts.append(e0.elapsed_time(e1))
+            assert int(outq.item()) == r_tv["max_pairs"], f"q={qq} disagrees"
+            qsweep[str(qq)] = {"ms": min(ts), "cells_per_s": cells / (min(ts) * 1e-3),
+                               "lookups": metrics.lookups(n, qq)}
+            fq.close()
+        best = min(qsweep, key=lambda k: qsweep[k]["ms"])
+        qsweep["best_q"] = int(best)
+
+    # ---- CPU baselines on bounded samples (rank 0, N = 1 only)
     cpu = None
+    cpu_tv = None
     if not a.no_cpu and rank == 0 and world == 1:
         prefix = min(n, 4000)
         full_s, dt = cpu_oracle_sample(seq, prefix)
         cpu = {"value": cells / full_s, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"cubic oracle (single-threaded C, Eq. 1) on the first {prefix} of the {n} bases took "
                          f"{dt:.2f} s; time scaled by ({n}/{prefix})^3 to one full fold ({full_s:.1f} s)"}
+        prefix2 = min(n, 3000)
+        full2, dt2 = cpu_two_vector_sample(seq, prefix2, q)
+        cpu_tv = {"value": cells / full2, "unit": UNIT, "cores": 1, "kind": "oracle two-vector (Algorithm 1)",
+                  "sample": f"single-threaded C Algorithm 1, q={q}, on the first {prefix2} bases took {dt2:.2f} s; "
+                            f"scaled by ({n}/{prefix2})^3 to one full fold ({full2:.1f} s)"}
 
     clocks = r_tv["clocks"] or {}
     sm_mhz = clocks.get("sm_mhz") or 2032.0
@@ -456,7 +504,7 @@ def main():
         "plain": {"ms_per_step": pl_ms, "cells_per_s": cells / (pl_ms * 1e-3),
                   "two_vector_speedup": pl_ms / statistics.mean(r_tv["step_ms"]),
                   "kernel_ms": statistics.mean(r_pl["kern_ms"])},
-        "batch": batch, "serve": serve,
+        "batch": batch, "serve": serve, "q_sweep": qsweep, "cpu_two_vector": cpu_tv,
         "max_pairs": r_tv["max_pairs"],
     }
     if rank == 0:

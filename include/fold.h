@@ -169,6 +169,41 @@ int fold_score_dev(fold_ctx *ctx, const uint8_t *d_codes, int32_t n, void *d_ws,
 int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int32_t *lens,
                int32_t *max_pairs_out, int16_t *const *D_out);
 
+/* Autotuner.  The paper fixes q per run and has no rule for the GPU's launch
+ * shapes, so they are measured.
+ * fold_tune: for this context (its q and method) and length n, times every
+ *   single-fold layout (one shared task queue; tile-only CTAs; column mode with
+ *   4 or 8 columns per tile CTA) with three middle-block chunk sizes, `reps`
+ *   timed folds each (1..100) after one warm-up, on a seeded synthetic uniform
+ *   sequence of length n, all on the context's stream (synchronous).  The
+ *   fastest is kept for n's size bucket (four per doubling) and used by later
+ *   single folds of that size unless FOLD_OPT_NEAR_CTAS, FOLD_OPT_COLUMNS or
+ *   FOLD_OPT_KCHUNK is set.  `out` receives the settings (as option values:
+ *   near_ctas -1/0/k, columns -1/0/v, kchunk 0 = automatic), their time in ms,
+ *   and the time of the automatic choice.  FOLD_EAGAIN while serving.
+ * fold_tune_q: picks q in [q_min, q_max] (2..10) for pair_mask and method
+ *   (0 two-vector, 1 plain: q 8 only) on `device`: with count == 1 it tunes a
+ *   context per q for length lens[0]; with count > 1 it times fold_batch on a
+ *   synthetic batch with lengths lens[0..count) (best of 3 wall-clock runs).
+ *   `out` is the fastest q's result.  Creates and destroys its own contexts.
+ * fold_tune_save / fold_tune_load: write / read the context's tuned entries
+ *   to / from a text file, one line per entry, tagged with the device name, q
+ *   and method; save keeps other tags' lines.  Load returns FOLD_EINVAL when
+ *   the file has no entry for this device, q and method. */
+typedef struct fold_tune_result {
+    int32_t q;
+    int32_t near_ctas;   /* FOLD_OPT_NEAR_CTAS value of the winner */
+    int32_t columns;     /* FOLD_OPT_COLUMNS value of the winner */
+    int32_t kchunk;      /* FOLD_OPT_KCHUNK value of the winner (0 = automatic) */
+    float ms;            /* its fold time */
+    float default_ms;    /* the automatic choice's fold time */
+} fold_tune_result;
+int fold_tune(fold_ctx *ctx, int32_t n, int32_t reps, fold_tune_result *out);
+int fold_tune_q(int device, uint16_t pair_mask, int method, const int32_t *lens, int32_t count, int32_t q_min,
+                int32_t q_max, fold_tune_result *out);
+int fold_tune_save(fold_ctx *ctx, const char *path);
+int fold_tune_load(fold_ctx *ctx, const char *path);
+
 /* Allocation-free fold.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc when they fold -- code
  * running inside a framework whose own allocator must own all device memory,

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <new>
@@ -126,9 +127,28 @@ int grid_for(fold_ctx *ctx) {
 // about 2e10 split points per ms, on 148 SMs) spread over the SMs left to chunks; the fastest wins.
 // The options force a layout: FOLD_OPT_NEAR_CTAS (0 = one queue, k = k tile CTAs) and
 // FOLD_OPT_COLUMNS (0 = no column mode, v = column mode with v columns per tile CTA).
-SplitPlan plan_split(fold_ctx *ctx, int NT, int grid, bool layout_ok) {
+// Size buckets of the tuned settings: four per doubling of n.
+int tune_bucket(int n) { return n < 1 ? 0 : (int)std::floor(4.0 * std::log2((double)n)); }
+
+FoldOpts single_opts(const fold_ctx *ctx, int n) {
+    FoldOpts o;
+    o.near_opt = ctx->near_ctas_opt;
+    o.cols_opt = ctx->columns_opt;
+    o.kc = ctx->kc_override;
+    if (o.near_opt == -1 && o.cols_opt == -1 && o.kc == 0) {
+        auto it = ctx->tune.find(tune_bucket(n));
+        if (it != ctx->tune.end()) {
+            o.near_opt = it->second.near_opt;
+            o.cols_opt = it->second.cols_opt;
+            o.kc = it->second.kc;
+        }
+    }
+    return o;
+}
+
+SplitPlan plan_split(fold_ctx *ctx, const FoldOpts &o, int NT, int grid, bool layout_ok) {
     SplitPlan sp;
-    const int nopt = ctx->near_ctas_opt, copt = ctx->columns_opt;
+    const int nopt = o.near_opt, copt = o.cols_opt;
     if (nopt == 0 || NT < 2 || grid < 2) return sp;
     auto ceil_div = [](int a, int b) { return (a + b - 1) / b; };
     auto column = [&](int cpc, int near) -> bool {
@@ -270,9 +290,10 @@ bool encode_seq(const char *seq, int n, uint8_t *out) {
 int single_schedule(fold_ctx *ctx, int n, const Plan &pl, const int4 **tasks, int *ntasks, int *nnear,
                     bool *layout_ok, const SeqDesc **d_sd) {
     int NT = pl.NTs[0];
-    int kc = ctx->kc_override > 0 ? ctx->kc_override : kc_auto(NT);
+    const FoldOpts o = single_opts(ctx, n);
+    int kc = o.kc > 0 ? o.kc : kc_auto(NT);
     // the split list is the same for every split layout; layout_ok is assumed for the choice here
-    const int nearc = plan_split(ctx, NT, grid_for(ctx), true).near_ctas;
+    const int nearc = plan_split(ctx, o, NT, grid_for(ctx), true).near_ctas;
     long long key = ((((long long)n << 24) | ((long long)ctx->method << 20) | ((long long)ctx->q << 16) | kc) << 12) |
                     (nearc & 0xfff);
     if (ctx->test_drop_task) key = -key - 1;   // separate cache entry for the fault-injection schedule
@@ -333,7 +354,7 @@ int enqueue_single(fold_ctx *ctx, const uint8_t *d_codes, int n, uint8_t *ws, si
         if (e != cudaSuccess) return status_from_cuda(e);
         FoldParams p = make_params(ctx, pl, ws, tasks, ntasks, d_sd);
         if (nnear > 0) {
-            const SplitPlan sp = plan_split(ctx, pl.NTs[0], grid_for(ctx), layout_ok);
+            const SplitPlan sp = plan_split(ctx, single_opts(ctx, n), pl.NTs[0], grid_for(ctx), layout_ok);
             p.col_mode = sp.col_mode;
             p.cols_per_cta = sp.cpc;
             p.nnear = nnear;

@@ -37,6 +37,21 @@ struct ServeState;  // serve.cu
 
 }  // namespace fold
 
+namespace fold {
+struct TuneEntry {
+    int near_opt = -1;   // FOLD_OPT_NEAR_CTAS value
+    int cols_opt = -1;   // FOLD_OPT_COLUMNS value
+    int kc = 0;          // FOLD_OPT_KCHUNK value (0: automatic)
+    float ms = 0.f;      // measured fold time
+};
+// Settings a single fold of one size runs with: the options if any is set, else the tuned entry
+// of the size's bucket, else automatic.
+struct FoldOpts {
+    int near_opt = -1, cols_opt = -1, kc = 0;
+};
+int tune_bucket(int n);
+}  // namespace fold
+
 struct fold_ctx {
     int device = 0;
     int q = 8;
@@ -50,6 +65,9 @@ struct fold_ctx {
     int test_drop_task = 0;
     int near_ctas_opt = -1;    // -1 automatic, 0 one shared queue, k > 0 k tile-only CTAs
     int columns_opt = -1;      // -1 automatic, 0 off, v >= 1 column mode with v columns per tile CTA
+    // tuned single-fold settings per size bucket (fold_tune / fold_tune_load); used when no option
+    // forces a layout or a chunk size
+    std::map<int, fold::TuneEntry> tune;
     cudaStream_t stream = nullptr;
     uint8_t *d_rcanon = nullptr;
     uint8_t *d_rpacked_buf = nullptr;
@@ -81,7 +99,10 @@ struct SplitPlan {
     int col_mode = 0;    // 1: column mode
     int cpc = kWarpsPerCta;   // columns per tile CTA in column mode
 };
-SplitPlan plan_split(fold_ctx *ctx, int NT, int grid, bool layout_ok);
+SplitPlan plan_split(fold_ctx *ctx, const FoldOpts &o, int NT, int grid, bool layout_ok);
+FoldOpts single_opts(const fold_ctx *ctx, int n);
+int enqueue_single(fold_ctx *ctx, const uint8_t *d_codes, int n, uint8_t *ws, size_t ws_bytes, int32_t *d_out,
+                   int16_t *d_D, cudaStream_t st);
 int split_queues(std::vector<int4> &tasks);
 bool encode_seq(const char *seq, int n, uint8_t *out);
 int ensure_buf(DevBuf &b, size_t bytes);

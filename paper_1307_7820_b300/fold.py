@@ -31,7 +31,7 @@ ABI_SYMBOLS = (
     "fold_init", "fold_destroy", "fold_strerror", "fold_set_option", "fold_get_option", "fold_rtable",
     "fold_score", "fold_workspace_bytes", "fold_score_dev", "fold_batch",
     "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop", "fold_trace_copy",
-    "fold_score_static", "fold_schedule_check",
+    "fold_score_static", "fold_schedule_check", "fold_tune", "fold_tune_q", "fold_tune_save", "fold_tune_load",
 )
 
 
@@ -41,6 +41,17 @@ class TraceRec(ctypes.Structure):
                 ("I", ctypes.c_int32), ("J", ctypes.c_int32), ("seq", ctypes.c_int32),
                 ("t_start", ctypes.c_int64), ("t_deps", ctypes.c_int64), ("t_mid", ctypes.c_int64),
                 ("t_end", ctypes.c_int64), ("t_aux", ctypes.c_int64 * 3)]
+
+
+
+class TuneResult(ctypes.Structure):
+    """struct fold_tune_result"""
+    _fields_ = [("q", ctypes.c_int32), ("near_ctas", ctypes.c_int32), ("columns", ctypes.c_int32),
+                ("kchunk", ctypes.c_int32), ("ms", ctypes.c_float), ("default_ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
 
 _lib = None
 
@@ -86,6 +97,12 @@ def lib():
     L.fold_schedule_check.argtypes = [i32, ctypes.c_int, ctypes.c_int, i32]
     L.fold_schedule_check.restype = ctypes.c_int
     L.fold_trace_copy.restype = i64
+    L.fold_tune.argtypes = [vp, i32, i32, P(TuneResult)]
+    L.fold_tune_q.argtypes = [ctypes.c_int, u16, ctypes.c_int, P(i32), i32, i32, i32, P(TuneResult)]
+    L.fold_tune_save.argtypes = [vp, ctypes.c_char_p]
+    L.fold_tune_load.argtypes = [vp, ctypes.c_char_p]
+    for name in ("fold_tune", "fold_tune_q", "fold_tune_save", "fold_tune_load"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("fold_set_option", "fold_get_option", "fold_rtable", "fold_score", "fold_score_dev", "fold_batch",
                  "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop"):
         getattr(L, name).restype = ctypes.c_int
@@ -191,6 +208,30 @@ def fold_schedule_check(n: int, q: int = 8, method: int = FOLD_METHOD_TWO_VECTOR
     return lib().fold_schedule_check(n, q, method, kchunk)
 
 
+def fold_tune(ctx: int, n: int, reps: int = 3) -> dict:
+    """Times the single-fold settings for length n; the fastest is kept for that size."""
+    r = TuneResult()
+    _check(lib().fold_tune(ctx, n, reps, ctypes.byref(r)), "fold_tune")
+    return r.as_dict()
+
+
+def fold_tune_q(lens, q_min: int = 4, q_max: int = 10, pair_mask: int = FOLD_PAIRS_DEFAULT,
+                method: int = FOLD_METHOD_TWO_VECTOR, device: int = 0) -> dict:
+    """Fastest q for one length (tuned) or a batch of lengths (timed fold_batch)."""
+    arr = (ctypes.c_int32 * len(lens))(*[int(x) for x in lens])
+    r = TuneResult()
+    _check(lib().fold_tune_q(device, pair_mask, method, arr, len(lens), q_min, q_max, ctypes.byref(r)), "fold_tune_q")
+    return r.as_dict()
+
+
+def fold_tune_save(ctx: int, path: str) -> None:
+    _check(lib().fold_tune_save(ctx, path.encode()), "fold_tune_save")
+
+
+def fold_tune_load(ctx: int, path: str) -> None:
+    _check(lib().fold_tune_load(ctx, path.encode()), "fold_tune_load")
+
+
 def fold_serve_start(ctx: int, budget_bytes: int, max_inflight: int = 4096) -> None:
     _check(lib().fold_serve_start(ctx, budget_bytes, max_inflight), "fold_serve_start")
 
@@ -254,6 +295,9 @@ class Folder:
 
     def batch(self, seqs, want_D: bool = False):
         return fold_batch(self.ctx, seqs, want_D)
+
+    def tune(self, n: int, reps: int = 3) -> dict:
+        return fold_tune(self.ctx, n, reps)
 
     def workspace_bytes(self, n: int) -> int:
         return fold_workspace_bytes(self.ctx, n)

@@ -51,6 +51,15 @@ def test_null_and_range_arguments(L):
     assert L.fold_set_option(None, fold.FOLD_OPT_METHOD, 0) == fold.FOLD_EINVAL
     assert L.fold_workspace_bytes(None, 10) == -fold.FOLD_EINVAL
     assert L.fold_batch(None, 1, None, None, None, None) == fold.FOLD_EINVAL
+    r = fold.TuneResult()
+    assert L.fold_tune(None, 100, 3, ctypes.byref(r)) == fold.FOLD_EINVAL
+    lens = (ctypes.c_int32 * 1)(100)
+    assert L.fold_tune_q(0, 0x5A48, 0, lens, 1, 9, 8, ctypes.byref(r)) == fold.FOLD_EINVAL   # empty q range
+    assert L.fold_tune_q(0, 0x5A48, 0, lens, 1, 1, 8, ctypes.byref(r)) == fold.FOLD_EINVAL   # q below 2
+    assert L.fold_tune_q(0, 0x5A48, 2, lens, 1, 8, 8, ctypes.byref(r)) == fold.FOLD_EINVAL   # unknown method
+    assert L.fold_tune_q(0, 0x5A48, 0, lens, 0, 8, 8, ctypes.byref(r)) == fold.FOLD_EINVAL   # no lengths
+    assert L.fold_tune_save(None, b"/tmp/x") == fold.FOLD_EINVAL
+    assert L.fold_tune_load(None, b"/tmp/x") == fold.FOLD_EINVAL
 
 
 def test_pair_mask_constants():
