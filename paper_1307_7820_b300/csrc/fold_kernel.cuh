@@ -957,7 +957,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 
     unsigned vhist = 0;        // vertical differences, newest in bit 0
     // residual window (two-vector): win[e] = D(IT+r+1+e, j) while row r is being computed
-    constexpr int NW = Q > 2 ? Q - 2 : 1;
+    constexpr int NW = Q > 1 ? Q - 1 : 1;
     int win[NW];
 #pragma unroll
     for (int e = 0; e < NW; ++e) win[e] = 0;
@@ -967,20 +967,22 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     // every candidate is evaluated with in-range indices and the invalid ones are masked
     auto old_terms = [&](int rr) -> int {
         if constexpr (TV) {
-            constexpr int NC = 1 + (Q > 2 ? Q - 2 : 0) + G;
+            constexpr int NC = 1 + (Q - 1) + G;
             int cand[NC];
             int k = 0;
             cand[k++] = (int)ws.pm[rr][c];
-            const int ce = (rr + Q - 1) / Q * Q;
-            // residual splits k in [i+2, IT+ce] (k = i+1 is the fresh D(i+1,j) term)
+            // residual splits k in [i+2, IT+ce], ce the end of the first group starting after row rr
+            // (k = i+1 is the D(i+1,j) term of the row loop); on a group's first row they cover that
+            // whole group, so no term of a row waits on the group its previous row completes
+            const int ce = (rr / Q + 1) * Q;
 #pragma unroll
-            for (int e = 0; e < Q - 2; ++e) {
+            for (int e = 0; e < Q - 1; ++e) {
                 const int kk = rr + 2 + e;
                 const int ix = min(kk, T);
                 const int v = (int)dg[rr][ix - 1] + win[e];
                 cand[k++] = (kk <= ce) ? v : kNeg16;
             }
-            // full groups of tile column I completed before row rr+1 (g*q > rr)
+            // full groups of tile column I after that one (g*q > rr), complete before row rr+1
 #pragma unroll
             for (int gl = 0; gl < G; ++gl) {
                 const uint32_t f = drf[rr][gl];
@@ -1045,9 +1047,9 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         // tile's own column D(IT+c'+1, j), valid for r <= c' < c
 #pragma unroll 1
         for (int r = T - 1; r >= 0; --r) {
-                const int pb = (int)((pbits >> r) & 1u);
-            int bl = __shfl_up_sync(FULL, below, 1);
-            bl = (c == 0) ? 0 : bl;
+            const int pb = (int)((pbits >> r) & 1u);
+            const int blraw = __shfl_up_sync(FULL, below, 1);
+            const int bl = (c == 0) ? 0 : blraw;
             int y = (c > r) ? pb + bl : (c == r ? 0 : kNeg16);
             y = valid ? y : kNeg16;
             ws.y[r & 1][c] = (int16_t)y;
@@ -1083,32 +1085,32 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         int yold = old_terms(T - 1);
 #pragma unroll 1
         for (int r = T - 1; r >= 0; --r) {
-                const int pb = (int)((pbits >> r) & 1u);
+            const int pb = (int)((pbits >> r) & 1u);
             // D(i+1, j-1): lane c-1's previous row; lane 0 reads the left column
-            int bl = __shfl_up_sync(FULL, below, 1);
-            const int lft = (int)ws.left[r + 1];
-            bl = (c == 0) ? lft : bl;
-            // fresh terms: pair, the split k = i+1 (D(i,i) + D(i+1,j)), and a group completed by row r+1
-            int y = max(max(yold, pb + bl), below);
-            if constexpr (TV) {
-                const int gl = r / Q;   // < G for every r < T; completed by row r+1 when r % Q == 0
-                const uint32_t f = drf[r][gl];
-                const uint32_t cb = last_cb;
-                const int v = rlookup<Q>(Rs, hrow_offset<Q>((int)(f & C::BMASK)), (int)(cb & C::BMASK));
-                const int cand = (int)(f >> 16) + (int)(cb >> 16) + v;
-                y = (r % Q == 0) ? max(y, cand) : y;
-            }
-            y = valid ? y : kNeg16;
-            // closure over the row: D_c = max(Y_c, max_{c'<c} Y_c' + W[c'][c])
-            ws.y[r & 1][c] = (int16_t)y;
+            const int blraw = __shfl_up_sync(FULL, below, 1);
+            const int bl = (c == 0) ? (int)ws.left[r + 1] : blraw;
+            // closure over the row, D_c = max(Y_c, max_{c'<c} Y_c' + W[c'][c]).  Only the pair term of
+            // Y_c' can matter there: every other term of Y_c' is a split D(i,k-1) + D(k,JT+c'), and with
+            // W[c'][c] added it is at most D(i,k-1) + D(k,j) (superadditivity, Eq. 1), a term Y_c or the
+            // closure already holds.  So the exchanged value is the pair term alone, a short chain.
+            const int v = (pb && valid) ? bl + 1 : kNeg16;
+            ws.y[r & 1][c] = (int16_t)v;
             __syncwarp();
+            // the closure's inputs go out first; the work below fills their latency
+            const uint4 *yp = reinterpret_cast<const uint4 *>(ws.y[r & 1]);
+            uint4 ya[4];
+#pragma unroll
+            for (int v4 = 0; v4 < 4; ++v4) ya[v4] = yp[v4];
+            // the terms that do not go through the closure: pair, the split k = i+1 (D(i,i) +
+            // D(i+1,j)), and the old terms
+            int y = max(max(yold, pb + bl), below);
+            y = valid ? y : kNeg16;
             // old terms of the next row overlap with this closure (the last one is unused)
             yold = old_terms(max(r - 1, 0));
-            const uint4 *yp = reinterpret_cast<const uint4 *>(ws.y[r & 1]);
             unsigned a0 = 0, a1 = 0, a2 = 0, a3 = 0;
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                const uint4 a = yp[v];
+                const uint4 a = ya[v];
                 a0 = __viaddmax_s16x2(a.x, Wp[4 * v + 0], a0);
                 a1 = __viaddmax_s16x2(a.y, Wp[4 * v + 1], a1);
                 a2 = __viaddmax_s16x2(a.z, Wp[4 * v + 2], a2);
@@ -1135,9 +1137,6 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         if (lane == 0 && nn_next > 0) cnt_next = ld_relaxed(P.cnt + sd.cnt_off + (I - 1) * NT + J);
     }
     if constexpr (TV) {
-        // horizontal difference vectors of the finished rows, packed with one ballot per row (bit c =
-        // D(i,JT+c) - D(i,JT+c-1)); the rows are independent, so their shuffle/ballot chains overlap
-        // all tile reads first (a ballot is a warp-synchronous point that loads are not moved across)
         bool up[T];
         int av[T];
 #pragma unroll
