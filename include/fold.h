@@ -169,6 +169,28 @@ int fold_score_dev(fold_ctx *ctx, const uint8_t *d_codes, int32_t n, void *d_ws,
 int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int32_t *lens,
                int32_t *max_pairs_out, int16_t *const *D_out);
 
+/* One optimal secondary structure (Section 2, traceback).  The paper stores
+ * D*(i,j), the argmax of Eq. 1, beside D; here the argmax is re-evaluated from
+ * the finished table at each cell the trace visits, by a one-block kernel, in a
+ * fixed order of preference: base i unpaired if D(i,j) = D(i+1,j); else the
+ * pair (i,j) if b(S_i,S_j) = 1 and D(i,j) = D(i+1,j-1) + 1; else the smallest
+ * split k in [i+2, j] with D(i,j) = D(i,k-1) + D(k,j).  The structure has
+ * D(0,n-1) pairs, no two of them cross, and every pair is allowed by the mask.
+ * fold_structure: host string in (as fold_score); max_pairs out; partner_out
+ *   (nullable, n int32): the base paired with each base or -1; dot_bracket_out
+ *   (nullable, n+1 chars): '(' / ')' for the smaller / larger base of each
+ *   pair, '.' otherwise, NUL-terminated.  Synchronous.
+ * fold_structure_workspace_bytes / fold_structure_dev: the device-resident
+ *   form (as fold_score_dev): d_ws of at least fold_structure_workspace_bytes(n)
+ *   bytes, 256-byte aligned; d_max_pairs one int32 (-FOLD_ETIMEOUT if the fold
+ *   failed, -FOLD_ECUDA if the trace found the table inconsistent); d_partner n
+ *   int32.  Enqueued on `stream` (NULL = the default stream). */
+int fold_structure(fold_ctx *ctx, const char *seq, int32_t n, int32_t *max_pairs, int32_t *partner_out,
+                   char *dot_bracket_out);
+int64_t fold_structure_workspace_bytes(fold_ctx *ctx, int32_t n);
+int fold_structure_dev(fold_ctx *ctx, const uint8_t *d_codes, int32_t n, void *d_ws, int64_t ws_bytes,
+                       int32_t *d_max_pairs, int32_t *d_partner, void *stream);
+
 /* Autotuner.  The paper fixes q per run and has no rule for the GPU's launch
  * shapes, so they are measured.
  * fold_tune: for this context (its q and method) and length n, times every

@@ -75,6 +75,8 @@ def _load():
         lib.oracle_rtable.restype = ctypes.c_long
         lib.oracle_two_vector.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_uint16, i32p, i64p]
         lib.oracle_two_vector.restype = ctypes.c_int
+        lib.oracle_traceback.argtypes = [u8p, ctypes.c_int, ctypes.c_uint16, i32p, i32p]
+        lib.oracle_traceback.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -112,6 +114,29 @@ def score(seq: str, mask: int = MASK6) -> int:
     if s < 0:
         raise MemoryError("oracle_nussinov_score failed")
     return int(s)
+
+
+def traceback(seq: str, mask: int = MASK6, D: np.ndarray | None = None) -> np.ndarray:
+    """Partner of each base (-1 unpaired) of one optimal structure: the argmax of Eq. 1 taken
+    at each visited cell in a fixed order of preference (unpaired, pair, smallest split)."""
+    lib = _load()
+    c = encode(seq)
+    n = len(c)
+    if D is None:
+        D = nussinov(seq, mask)
+    D = np.ascontiguousarray(D, dtype=np.int32)
+    partner = np.full(n, -1, dtype=np.int32)
+    if n:
+        rc = lib.oracle_traceback(_u8(c), n, mask, D.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                  partner.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        if rc < 0:
+            raise ValueError("the table admits no argmax: not a table of Eq. 1")
+    return partner
+
+
+def dot_bracket(partner: np.ndarray) -> str:
+    """'(' / ')' for the smaller / larger index of each pair, '.' for unpaired bases."""
+    return "".join("." if p < 0 else ("(" if p > k else ")") for k, p in enumerate(partner))
 
 
 def brute(seq: str, mask: int = MASK6) -> int:

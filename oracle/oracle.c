@@ -21,6 +21,9 @@
  *   oracle_two_vector   Section 3.1, Algorithm 1: column-wise fill with the
  *                       pair term, the two residual loops, the Four-Russians
  *                       loop of table lookups (Eq. 3), and the vector stores.
+ *   oracle_traceback    Section 2, the traceback: the argmax of Eq. 1 (D*)
+ *                       re-evaluated at each visited cell of a finished table,
+ *                       giving one optimal set of pairs.
  *
  * Conventions (the readings of the paper used throughout):
  *   - positions are 0-based; D(i,j) = 0 for i >= j; answer D(0,n-1);
@@ -258,4 +261,56 @@ int oracle_two_vector(const uint8_t *codes, int n, int q, uint16_t mask, int32_t
     free(hv);
     free(cv);
     return 0;
+}
+
+/* Section 2: traceback.  The paper keeps D*(i,j), the argmax of Eq. 1, beside
+ * D; here the argmax is re-evaluated from D at each cell the traceback visits,
+ * with a fixed order of preference so that the result is one definite optimal
+ * structure:
+ *   1. the split k = i+1 (base i left unpaired), if D(i,j) = D(i+1,j);
+ *   2. else the pair (i,j), if b(S_i,S_j) = 1 and D(i,j) = D(i+1,j-1) + 1;
+ *   3. else the smallest k in [i+2, j] with D(i,j) = D(i,k-1) + D(k,j).
+ * D: the n*n row-major table of oracle_nussinov (D(i,j) = 0 for i >= j).
+ * partner[x] = the base paired with x, or -1.  Returns the number of pairs,
+ * or -1 if the table admits no argmax somewhere (not a table of Eq. 1). */
+int oracle_traceback(const uint8_t *codes, int n, uint16_t mask, const int32_t *D, int32_t *partner) {
+    if (n <= 0) return 0;
+    for (int x = 0; x < n; ++x) partner[x] = -1;
+    int *stack = (int *)malloc(sizeof(int) * 2 * (size_t)(n + 1));
+    if (!stack) return -1;
+    int top = 0, pairs = 0;
+    stack[top++] = 0;
+    stack[top++] = n - 1;
+#define DV(a, b) ((a) >= (b) ? 0 : D[(size_t)(a) * n + (b)])
+    while (top > 0) {
+        int j = stack[--top];
+        int i = stack[--top];
+        while (i < j) {
+            const int dij = DV(i, j);
+            if (dij == DV(i + 1, j)) {            /* 1: i unpaired */
+                ++i;
+                continue;
+            }
+            if (pair_b(mask, codes[i], codes[j]) && dij == DV(i + 1, j - 1) + 1) {   /* 2: pair (i, j) */
+                partner[i] = j;
+                partner[j] = i;
+                ++pairs;
+                ++i;
+                --j;
+                continue;
+            }
+            int k = i + 2;                          /* 3: the smallest split */
+            while (k <= j && DV(i, k - 1) + DV(k, j) != dij) ++k;
+            if (k > j) {
+                free(stack);
+                return -1;
+            }
+            stack[top++] = k;
+            stack[top++] = j;
+            j = k - 1;
+        }
+    }
+#undef DV
+    free(stack);
+    return pairs;
 }

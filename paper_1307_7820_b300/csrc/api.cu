@@ -584,6 +584,78 @@ int fold_rtable(fold_ctx *ctx, uint8_t *out, int64_t cap) {
     return status_from_cuda(e);
 }
 
+// Structure workspace: the fold's, then the traceback's stack of pending intervals.
+static size_t structure_bytes(const Plan &pl, int n) {
+    return align_up(pl.bytes, 256) + align_up(sizeof(int2) * (size_t)std::max(n, 1), 256);
+}
+
+int64_t fold_structure_workspace_bytes(fold_ctx *ctx, int32_t n) {
+    if (!ctx || n < 0 || n > FOLD_MAX_N) return -FOLD_EINVAL;
+    Plan pl = make_plan(&n, 1, ctx->q, ctx->method);
+    return (int64_t)structure_bytes(pl, n);
+}
+
+int fold_structure_dev(fold_ctx *ctx, const uint8_t *d_codes, int32_t n, void *d_ws, int64_t ws_bytes,
+                       int32_t *d_max_pairs, int32_t *d_partner, void *stream) {
+    if (!ctx || !d_ws || !d_max_pairs || n < 0 || n > FOLD_MAX_N || (n > 0 && (!d_codes || !d_partner)))
+        return FOLD_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_ws) & 255) != 0) return FOLD_EINVAL;
+    cudaSetDevice(ctx->device);
+    Plan pl = make_plan(&n, 1, ctx->q, ctx->method);
+    if (ws_bytes < 0 || (size_t)ws_bytes < structure_bytes(pl, n)) return FOLD_ENOMEM;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t *ws = reinterpret_cast<uint8_t *>(d_ws);
+    int rc = enqueue_single(ctx, d_codes, n, ws, pl.bytes, d_max_pairs, nullptr, st);
+    if (rc) return rc;
+    if (n == 1) return status_from_cuda(cudaMemsetAsync(d_partner, 0xff, sizeof(int32_t), st));
+    if (n >= 2) {
+        int2 *stack = reinterpret_cast<int2 *>(ws + align_up(pl.bytes, 256));
+        cudaError_t e = launch_traceback(reinterpret_cast<const int16_t *>(ws + pl.off_drow), pl.sd[0].Np,
+                                         ws + pl.off_codes, n, ctx->pair64, stack, d_partner, d_max_pairs, FOLD_ECUDA, st);
+        if (e != cudaSuccess) return status_from_cuda(e);
+        ctx->launches += 1;
+    }
+    return FOLD_OK;
+}
+
+int fold_structure(fold_ctx *ctx, const char *seq, int32_t n, int32_t *max_pairs, int32_t *partner_out,
+                   char *dot_bracket_out) {
+    if (!ctx || !max_pairs || n < 0 || n > FOLD_MAX_N || (n > 0 && !seq)) return FOLD_EINVAL;
+    cudaSetDevice(ctx->device);
+    const size_t nn = (size_t)std::max(n, 1);
+    size_t hbytes = align_up(nn, 64) + 64 + 4 * nn;
+    if (ensure_host(ctx->hstage, hbytes)) return FOLD_ENOMEM;
+    uint8_t *hcodes = reinterpret_cast<uint8_t *>(ctx->hstage.ptr);
+    int32_t *hres = reinterpret_cast<int32_t *>(hcodes + align_up(nn, 64));
+    int32_t *hpart = hres + 16;
+    if (!encode_seq(seq, n, hcodes)) return FOLD_EINVAL;
+    Plan pl = make_plan(&n, 1, ctx->q, ctx->method);
+    const size_t wsb = structure_bytes(pl, n);
+    size_t aux_bytes = align_up(nn, 256) + 256 + align_up(4 * nn, 256);
+    if (ensure_buf(ctx->ws, wsb) || ensure_buf(ctx->aux, aux_bytes)) return FOLD_ENOMEM;
+    uint8_t *dcodes = reinterpret_cast<uint8_t *>(ctx->aux.ptr);
+    int32_t *dres = reinterpret_cast<int32_t *>(dcodes + align_up(nn, 256));
+    int32_t *dpart = reinterpret_cast<int32_t *>(dcodes + align_up(nn, 256) + 256);
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaSuccess;
+    if (n > 0) e = cudaMemcpyAsync(dcodes, hcodes, (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    int rc = fold_structure_dev(ctx, dcodes, n, ctx->ws.ptr, (int64_t)ctx->ws.bytes, dres, dpart, st);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(hres, dres, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(hpart, dpart, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    if (*hres < 0) return -*hres == FOLD_ETIMEOUT ? FOLD_ETIMEOUT : FOLD_ECUDA;
+    *max_pairs = *hres;
+    if (partner_out && n > 0) memcpy(partner_out, hpart, sizeof(int32_t) * (size_t)n);
+    if (dot_bracket_out) {
+        for (int32_t x = 0; x < n; ++x) dot_bracket_out[x] = hpart[x] < 0 ? '.' : (hpart[x] > x ? '(' : ')');
+        dot_bracket_out[n] = '\0';
+    }
+    return FOLD_OK;
+}
+
 int64_t fold_workspace_bytes(fold_ctx *ctx, int32_t n) {
     if (!ctx || n < 0 || n > FOLD_MAX_N) return -FOLD_EINVAL;
     Plan pl = make_plan(&n, 1, ctx->q, ctx->method);

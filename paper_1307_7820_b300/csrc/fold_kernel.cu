@@ -113,6 +113,101 @@ int fold_blocks_per_sm(int q, int method) {
     return 0;
 }
 
+// ------------------------------------------------------------------ traceback
+// Section 2: one optimal structure from a finished table.  The paper keeps D* (the argmax of Eq. 1)
+// beside D; here the argmax is re-evaluated from D at each cell visited, in a fixed order of
+// preference: the split k = i+1 (base i unpaired) if D(i,j) = D(i+1,j); else the pair (i,j) if
+// b(S_i,S_j) = 1 and D(i,j) = D(i+1,j-1) + 1; else the smallest k in [i+2, j] with D(i,j) =
+// D(i,k-1) + D(k,j).  One block: thread 0 follows unpaired bases and pairs (each step reads two
+// cells), the whole block searches a split's k range, blockDim candidates at a time.  The pending
+// intervals live in `stack` (n entries).  partner[x] = the base paired with x, or -1.  *result is
+// the fold's answer D(0,n-1) (or -status if the fold failed, then nothing is traced); it becomes
+// -fail_code if the trace finds no argmax somewhere, runs past its step bound, or ends with a
+// different number of pairs (the table would not be one of Eq. 1).
+__global__ void traceback_kernel(const int16_t *Drow, int Np, const uint8_t *codes, int n, unsigned long long pair64,
+                                 int2 *stack, int32_t *partner, int32_t *result, int fail_code) {
+    __shared__ int s_i, s_j, s_dij, s_k, s_act;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int x = tid; x < n; x += nt) partner[x] = -1;
+    // the fold failed (its answer is -status): no table to trace
+    if (*(volatile const int32_t *)result < 0) return;
+    int status = 0, pairs = 0;   // thread 0's
+    auto DV = [&](int a, int b) -> int { return a >= b ? 0 : (int)Drow[(size_t)a * Np + b]; };
+    int top = 0, steps = 0;   // thread 0's stack depth and step count
+    int ci = 0, cj = n - 1;   // thread 0's current interval (empty when ci >= cj)
+    __syncthreads();
+    for (;;) {
+        if (tid == 0) {
+            int act = 0;   // 0: finished, 2: a split to search
+            for (;;) {
+                if (ci >= cj) {
+                    if (top == 0) break;
+                    const int2 e = stack[--top];
+                    ci = e.x;
+                    cj = e.y;
+                    continue;
+                }
+                if (++steps > 4 * n + 8) {
+                    status = 1;
+                    break;
+                }
+                const int dij = DV(ci, cj);
+                if (dij == DV(ci + 1, cj)) {   // base ci unpaired
+                    ++ci;
+                    continue;
+                }
+                if (((pair64 >> (8 * codes[ci] + codes[cj])) & 1ull) && dij == DV(ci + 1, cj - 1) + 1) {
+                    partner[ci] = cj;
+                    partner[cj] = ci;
+                    ++pairs;
+                    ++ci;
+                    --cj;
+                    continue;
+                }
+                s_i = ci;
+                s_j = cj;
+                s_dij = dij;
+                s_k = 0x7fffffff;
+                act = 2;
+                break;
+            }
+            s_act = act;
+        }
+        __syncthreads();
+        if (s_act == 0) break;
+        const int i = s_i, j = s_j, dij = s_dij;
+        for (int base = i + 2; base <= j; base += nt) {
+            const int k = base + tid;
+            if (k <= j && DV(i, k - 1) + DV(k, j) == dij) atomicMin(&s_k, k);
+            __syncthreads();
+            const bool found = s_k != 0x7fffffff;
+            __syncthreads();
+            if (found) break;
+        }
+        if (tid == 0) {
+            const int k = s_k;
+            if (k == 0x7fffffff || top >= n) {   // no argmax: stop
+                status = 2;
+                ci = cj = 0;
+                top = 0;
+            } else {
+                stack[top++] = make_int2(k, j);
+                ci = i;
+                cj = k - 1;
+            }
+        }
+        __syncthreads();
+    }
+    // a structure with as many pairs as the answer, or the answer becomes -fail_code
+    if (tid == 0 && (status != 0 || pairs != *result)) *result = -fail_code;
+}
+
+cudaError_t launch_traceback(const int16_t *drow, int Np, const uint8_t *codes, int n, unsigned long long pair64,
+                             int2 *stack, int32_t *partner, int32_t *result, int fail_code, cudaStream_t st) {
+    traceback_kernel<<<1, 256, 0, st>>>(drow, Np, codes, n, pair64, stack, partner, result, fail_code);
+    return cudaGetLastError();
+}
+
 // Writes the answers (or -status if any device-side wait failed).
 __global__ void finalize_kernel(const int *error, const int *results, int count, int32_t *out) {
     int e = *(volatile const int *)error;

@@ -32,6 +32,7 @@ ABI_SYMBOLS = (
     "fold_score", "fold_workspace_bytes", "fold_score_dev", "fold_batch",
     "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop", "fold_trace_copy",
     "fold_score_static", "fold_schedule_check", "fold_tune", "fold_tune_q", "fold_tune_save", "fold_tune_load",
+    "fold_structure", "fold_structure_workspace_bytes", "fold_structure_dev",
 )
 
 
@@ -97,6 +98,12 @@ def lib():
     L.fold_schedule_check.argtypes = [i32, ctypes.c_int, ctypes.c_int, i32]
     L.fold_schedule_check.restype = ctypes.c_int
     L.fold_trace_copy.restype = i64
+    L.fold_structure.argtypes = [vp, ctypes.c_char_p, i32, P(i32), vp, vp]
+    L.fold_structure.restype = ctypes.c_int
+    L.fold_structure_workspace_bytes.argtypes = [vp, i32]
+    L.fold_structure_workspace_bytes.restype = i64
+    L.fold_structure_dev.argtypes = [vp, vp, i32, vp, i64, vp, vp, vp]
+    L.fold_structure_dev.restype = ctypes.c_int
     L.fold_tune.argtypes = [vp, i32, i32, P(TuneResult)]
     L.fold_tune_q.argtypes = [ctypes.c_int, u16, ctypes.c_int, P(i32), i32, i32, i32, P(TuneResult)]
     L.fold_tune_save.argtypes = [vp, ctypes.c_char_p]
@@ -208,6 +215,30 @@ def fold_schedule_check(n: int, q: int = 8, method: int = FOLD_METHOD_TWO_VECTOR
     return lib().fold_schedule_check(n, q, method, kchunk)
 
 
+def fold_structure(ctx: int, seq: str):
+    """(max pairs, partner array int32, dot-bracket string) of one optimal structure."""
+    b = seq.encode("ascii")
+    n = len(b)
+    mp = ctypes.c_int32()
+    partner = np.full(max(n, 1), -1, dtype=np.int32)
+    db = ctypes.create_string_buffer(n + 1)
+    _check(lib().fold_structure(ctx, b, n, ctypes.byref(mp), partner.ctypes.data, db), "fold_structure")
+    return mp.value, partner[:n], db.value.decode("ascii")
+
+
+def fold_structure_workspace_bytes(ctx: int, n: int) -> int:
+    r = lib().fold_structure_workspace_bytes(ctx, n)
+    if r < 0:
+        raise FoldError(-r, "fold_structure_workspace_bytes")
+    return r
+
+
+def fold_structure_dev(ctx: int, d_codes: int | None, n: int, d_ws: int, ws_bytes: int, d_max_pairs: int,
+                       d_partner: int | None, stream: int | None = None) -> None:
+    _check(lib().fold_structure_dev(ctx, d_codes, n, d_ws, ws_bytes, d_max_pairs, d_partner, stream),
+           "fold_structure_dev")
+
+
 def fold_tune(ctx: int, n: int, reps: int = 3) -> dict:
     """Times the single-fold settings for length n; the fastest is kept for that size."""
     r = TuneResult()
@@ -295,6 +326,10 @@ class Folder:
 
     def batch(self, seqs, want_D: bool = False):
         return fold_batch(self.ctx, seqs, want_D)
+
+    def structure(self, seq: str):
+        """(max pairs, partner array, dot-bracket) of one optimal structure."""
+        return fold_structure(self.ctx, seq)
 
     def tune(self, n: int, reps: int = 3) -> dict:
         return fold_tune(self.ctx, n, reps)
