@@ -80,9 +80,12 @@ enum fold_option {
     FOLD_OPT_TRACE = 11,      /* 1 = record per-task timestamps (see fold_trace_copy); 0 = off */
     FOLD_OPT_NEAR_CTAS = 12,  /* single folds: CTAs that run only tile tasks while the others run only
                                  middle-block chunks; -1 = automatic (default), 0 = one shared queue */
-    FOLD_OPT_COLUMNS = 13     /* with tile-only CTAs: each warp owns one tile column and computes it
+    FOLD_OPT_COLUMNS = 13,    /* with tile-only CTAs: each warp owns one tile column and computes it
                                  bottom-up (needs ceil(n_tiles / v) tile CTAs); -1 = automatic
                                  (default, v = 8), 0 = off, v = 1..8 = on, v columns per tile CTA */
+    FOLD_OPT_BATCH_FLAT = 14  /* fold_batch's middle-block chunks: -1 = automatic / 1 = fixed size
+                                 (FOLD_OPT_KCHUNK, default 64 blocks), 0 = the single fold's sizes
+                                 (growing from both ends of each range) */
 };
 
 /* One record per task of the last traced persistent launch. */

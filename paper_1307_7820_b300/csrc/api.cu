@@ -497,6 +497,10 @@ int fold_set_option(fold_ctx *ctx, int option, int64_t value) {
             if (value < -1 || value > kWarpsPerCta) return FOLD_EINVAL;
             ctx->columns_opt = (int)value;
             return FOLD_OK;
+        case FOLD_OPT_BATCH_FLAT:
+            if (value < -1 || value > 1) return FOLD_EINVAL;
+            ctx->batch_flat_opt = (int)value;
+            return FOLD_OK;
     }
     return FOLD_EINVAL;
 }
@@ -516,6 +520,7 @@ int fold_get_option(fold_ctx *ctx, int option, int64_t *value) {
         case FOLD_OPT_TRACE: *value = ctx->trace; return FOLD_OK;
         case FOLD_OPT_NEAR_CTAS: *value = ctx->near_ctas_opt; return FOLD_OK;
         case FOLD_OPT_COLUMNS: *value = ctx->columns_opt; return FOLD_OK;
+        case FOLD_OPT_BATCH_FLAT: *value = ctx->batch_flat_opt; return FOLD_OK;
         case FOLD_OPT_KERNEL_NS: {
             if (!ctx->ev_pending) { *value = 0; return FOLD_OK; }
             float ms = 0.f;
@@ -713,13 +718,16 @@ int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int3
     Plan pl = make_plan(lens, count, ctx->q, ctx->method);
     int maxNT = 0;
     for (int v : pl.NTs) maxNT = std::max(maxNT, v);
-    int kc = ctx->kc_override > 0 ? ctx->kc_override : kc_auto(maxNT);
-    std::vector<int4> tv;
-    build_schedule(pl.NTs, kc, strip_of(ctx->q, ctx->method), tv);
-    // host staging: codes (padded) | SeqDesc | tasks | results
+    // a batch is bound by throughput, not by one fold's critical path: chunks of kc blocks each
+    // (fewer tasks) unless FOLD_OPT_BATCH_FLAT asks for the single-fold geometric sizes
+    const bool flat = ctx->batch_flat_opt != 0;
+    int kc = ctx->kc_override > 0 ? ctx->kc_override : (flat ? 64 : kc_auto(maxNT));
+    const int strip = strip_of(ctx->q, ctx->method);
+    const size_t ntasks = build_schedule_into(pl.NTs, kc, strip, !flat, nullptr, 0);
+    // host staging: codes (padded) | SeqDesc | tasks | results; the task list is written in place
     size_t codes_bytes = pl.off_drow - pl.off_codes;
     size_t sd_bytes = align_up(sizeof(SeqDesc) * count, 256);
-    size_t task_bytes = align_up(tv.size() * sizeof(int4), 256);
+    size_t task_bytes = align_up(ntasks * sizeof(int4), 256);
     size_t res_bytes = align_up(4 * (size_t)count, 256);
     if (ensure_host(ctx->hstage, codes_bytes + sd_bytes + task_bytes + res_bytes)) return FOLD_ENOMEM;
     uint8_t *h = reinterpret_cast<uint8_t *>(ctx->hstage.ptr);
@@ -728,7 +736,7 @@ int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int3
     for (int k = 0; k < count; ++k)
         if (!encode_seq(seqs[k], lens[k], hcodes + pl.sd[k].code_off)) return FOLD_EINVAL;
     memcpy(h + codes_bytes, pl.sd.data(), sizeof(SeqDesc) * count);
-    if (!tv.empty()) memcpy(h + codes_bytes + sd_bytes, tv.data(), tv.size() * sizeof(int4));
+    build_schedule_into(pl.NTs, kc, strip, !flat, reinterpret_cast<int4 *>(h + codes_bytes + sd_bytes), ntasks);
     int32_t *hres = reinterpret_cast<int32_t *>(h + codes_bytes + sd_bytes + task_bytes);
     if (ensure_buf(ctx->ws, pl.bytes) || ensure_buf(ctx->aux, sd_bytes + task_bytes + res_bytes)) return FOLD_ENOMEM;
     uint8_t *ws = reinterpret_cast<uint8_t *>(ctx->ws.ptr);
@@ -741,8 +749,8 @@ int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int3
     if (e == cudaSuccess) e = cudaMemcpyAsync(ws + pl.off_codes, hcodes, codes_bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(aux, h + codes_bytes, sd_bytes + task_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return status_from_cuda(e);
-    FoldParams p = make_params(ctx, pl, ws, d_tasks, (int)tv.size(), d_sd);
-    if (!tv.empty()) {
+    FoldParams p = make_params(ctx, pl, ws, d_tasks, (int)ntasks, d_sd);
+    if (ntasks > 0) {
         e = launch_fold_instrumented(ctx, p, st);
         if (e != cudaSuccess) return status_from_cuda(e);
         ctx->launches += 1;

@@ -25,6 +25,8 @@
 // task depends only on tasks placed earlier in the list, and workers take
 // tasks in list order, so the kernel can always make progress.
 #include <algorithm>
+#include <map>
+#include <thread>
 #include <vector>
 
 #include "fold_common.h"
@@ -39,9 +41,15 @@ struct Chunk { int type, I, J, Ka, Kb; };
 // to kc) from both ends toward the middle.  The blocks at either end of a
 // tile's middle range are the last to become ready (they need the most
 // recent tiles), so they come in small pieces that finish quickly; the middle
-// blocks, ready long before, form the big chunks.
-std::vector<std::pair<int, int>> split_range(int lo, int hi, int kc) {
+// blocks, ready long before, form the big chunks.  Without `geometric` the
+// chunks are kc blocks each (batches: the folds' own critical paths matter
+// little there, the number of tasks does).
+std::vector<std::pair<int, int>> split_range(int lo, int hi, int kc, bool geometric) {
     std::vector<std::pair<int, int>> head, tail;
+    if (!geometric) {
+        for (int a = lo; a <= hi; a += kc) head.push_back({a, std::min(hi, a + kc - 1)});
+        return head;
+    }
     int size = 1;
     while (lo <= hi) {
         const int a = std::min(size, hi - lo + 1);
@@ -58,80 +66,150 @@ std::vector<std::pair<int, int>> split_range(int lo, int hi, int kc) {
 }
 }
 
-void build_schedule(const std::vector<int> &NTs, int kc, int strip, std::vector<int4> &out) {
+namespace {
+// The task list of one sequence with NT tiles per side (sequence index 0), step by step: the NEAR
+// tasks of tile diagonal t are tasks[near_begin[t], chunk_begin[t]), the chunks placed after
+// them tasks[chunk_begin[t], near_begin[t+1]).
+struct SeqTemplate {
+    std::vector<int4> tasks;
+    std::vector<int> near_begin, chunk_begin;
+};
+
+void build_one(int NT, int kc, int S, bool geometric, SeqTemplate &tp) {
+    std::vector<std::vector<Chunk>> bucket(NT > 0 ? NT : 1);
+    std::vector<int> nfar((size_t)NT * NT, 0);
+    auto place = [&](int d) { return d + 1; };
+    // single-tile chunks
+    for (int t = 4; t < NT; ++t) {
+        for (int I = 0; I + t < NT; ++I) {
+            const int J = I + t;
+            const int J0 = J / S * S;
+            const bool has_strip = S > 1 && J0 - 2 >= I + S + 1;
+            int ranges[2][2] = {{I + 2, J - 2}, {1, 0}};
+            if (has_strip) {
+                ranges[0][0] = I + 2; ranges[0][1] = I + S;
+                ranges[1][0] = J0 - 1; ranges[1][1] = J - 2;
+            }
+            for (auto &rg : ranges) {
+                for (const auto &ck : split_range(rg[0], rg[1], kc, geometric)) {
+                    const int Ka = ck.first, Kb = ck.second;
+                    int d = std::max(Kb - I, J - Ka);
+                    if (t >= kRing) d = std::max(d, t - kRing);
+                    bucket[place(d)].push_back({kTaskFar, I, J, Ka, Kb});
+                    nfar[(size_t)I * NT + J]++;
+                }
+            }
+        }
+    }
+    // strip chunks over tiles (I, J0..J0+Seff-1)
+    if (S > 1) {
+        for (int I = 0; I < NT; ++I) {
+            for (int J0 = (I + S + 3 + S - 1) / S * S; J0 < NT; J0 += S) {
+                const int Seff = std::min(S, NT - J0);
+                const int Jl = J0 + Seff - 1;
+                for (const auto &ck : split_range(I + S + 1, J0 - 2, kc, geometric)) {
+                    const int Ka = ck.first, Kb = ck.second;
+                    int d = std::max(Kb - I, Jl - Ka);
+                    if (Jl - I >= kRing) d = std::max(d, Jl - I - kRing);
+                    bucket[place(d)].push_back({kTaskFarStrip, I, J0, Ka, Kb});
+                    for (int J = J0; J <= Jl; ++J) nfar[(size_t)I * NT + J]++;
+                }
+            }
+        }
+    }
+    // most urgent first: lower tile diagonal, then row
+    for (auto &bk : bucket)
+        std::stable_sort(bk.begin(), bk.end(), [](const Chunk &x, const Chunk &y) {
+            const int dx = x.J - x.I, dy = y.J - y.I;
+            return dx != dy ? dx < dy : x.I < y.I;
+        });
+    tp.near_begin.assign(NT + 1, 0);
+    tp.chunk_begin.assign(NT, 0);
+    for (int t = 0; t < NT; ++t) {
+        tp.near_begin[t] = (int)tp.tasks.size();
+        for (int I = 0; I + t < NT; ++I)
+            tp.tasks.push_back(make_int4(0, task_pack(kTaskNear, I, I + t), nfar[(size_t)I * NT + I + t], 0));
+        tp.chunk_begin[t] = (int)tp.tasks.size();
+        for (const Chunk &ck : bucket[t]) tp.tasks.push_back(make_int4(0, task_pack(ck.type, ck.I, ck.J), ck.Ka, ck.Kb));
+    }
+    tp.near_begin[NT] = (int)tp.tasks.size();
+}
+}  // namespace
+
+void build_schedule(const std::vector<int> &NTs, int kc, int strip, std::vector<int4> &out, bool geometric) {
     out.clear();
-    int nseq = (int)NTs.size();
+    out.resize(build_schedule_into(NTs, kc, strip, geometric, nullptr, 0));
+    build_schedule_into(NTs, kc, strip, geometric, out.data(), out.size());
+}
+
+size_t build_schedule_into(const std::vector<int> &NTs, int kc, int strip, bool geometric, int4 *out, size_t cap) {
+    const int nseq = (int)NTs.size();
     int maxNT = 0;
     for (int v : NTs) maxNT = std::max(maxNT, v);
     if (kc < 1) kc = 1;
     if (strip < 1) strip = 1;
-    const int S = strip;
-    std::vector<std::vector<std::vector<Chunk>>> bucket(nseq);
-    std::vector<std::vector<int>> nfar(nseq);
-    for (int s = 0; s < nseq; ++s) {
-        const int NT = NTs[s];
-        bucket[s].assign(NT > 0 ? NT : 1, {});
-        nfar[s].assign((size_t)NT * NT, 0);
-        auto place = [&](int d) { return d + 1; };
-        // single-tile chunks
-        for (int t = 4; t < NT; ++t) {
-            for (int I = 0; I + t < NT; ++I) {
-                const int J = I + t;
-                const int J0 = J / S * S;
-                const bool has_strip = S > 1 && J0 - 2 >= I + S + 1;
-                int ranges[2][2] = {{I + 2, J - 2}, {1, 0}};
-                if (has_strip) {
-                    ranges[0][0] = I + 2; ranges[0][1] = I + S;
-                    ranges[1][0] = J0 - 1; ranges[1][1] = J - 2;
-                }
-                for (auto &rg : ranges) {
-                    for (const auto &ck : split_range(rg[0], rg[1], kc)) {
-                        const int Ka = ck.first, Kb = ck.second;
-                        int d = std::max(Kb - I, J - Ka);
-                        if (t >= kRing) d = std::max(d, t - kRing);
-                        bucket[s][place(d)].push_back({kTaskFar, I, J, Ka, Kb});
-                        nfar[s][(size_t)I * NT + J]++;
-                    }
-                }
-            }
-        }
-        // strip chunks over tiles (I, J0..J0+Seff-1)
-        if (S > 1) {
-            for (int I = 0; I < NT; ++I) {
-                for (int J0 = (I + S + 3 + S - 1) / S * S; J0 < NT; J0 += S) {
-                    const int Seff = std::min(S, NT - J0);
-                    const int Jl = J0 + Seff - 1;
-                    for (const auto &ck : split_range(I + S + 1, J0 - 2, kc)) {
-                        const int Ka = ck.first, Kb = ck.second;
-                        int d = std::max(Kb - I, Jl - Ka);
-                        if (Jl - I >= kRing) d = std::max(d, Jl - I - kRing);
-                        bucket[s][place(d)].push_back({kTaskFarStrip, I, J0, Ka, Kb});
-                        for (int J = J0; J <= Jl; ++J) nfar[s][(size_t)I * NT + J]++;
-                    }
-                }
-            }
-        }
-        // most urgent first: lower tile diagonal, then row
-        for (auto &b : bucket[s])
-            std::stable_sort(b.begin(), b.end(), [](const Chunk &a, const Chunk &c) {
-                int da = a.J - a.I, dc = c.J - c.I;
-                return da != dc ? da < dc : a.I < c.I;
-            });
-    }
+    // one template per distinct size (a batch has few), then every sequence's copy interleaved:
+    // for each step t, the NEAR tasks of all sequences, then their chunks
+    std::map<int, SeqTemplate> tpl;
+    for (int v : NTs)
+        if (v > 0 && !tpl.count(v)) build_one(v, kc, strip, geometric, tpl[v]);
+    std::vector<const SeqTemplate *> tp((size_t)nseq, nullptr);
+    for (int q = 0; q < nseq; ++q)
+        if (NTs[q] > 0) tp[(size_t)q] = &tpl[NTs[q]];
+    size_t total = 0;
+    for (int q = 0; q < nseq; ++q)
+        if (tp[(size_t)q]) total += tp[(size_t)q]->tasks.size();
+    if (!out || cap < total) return total;
+    // segments of the output in order (one sequence's NEAR tasks or chunks of one step), then
+    // copied by a few threads when the list is long
+    struct Seg {
+        const int4 *src;
+        int count, seq;
+        size_t dst;
+    };
+    std::vector<Seg> segs;
+    size_t k = 0;
     for (int t = 0; t < maxNT; ++t) {
-        for (int s = 0; s < nseq; ++s) {
-            const int NT = NTs[s];
-            if (t >= NT) continue;
-            for (int I = 0; I + t < NT; ++I) {
-                const int J = I + t;
-                out.push_back(make_int4(s, task_pack(kTaskNear, I, J), nfar[s][(size_t)I * NT + J], 0));
+        for (int part = 0; part < 2; ++part) {
+            for (int q = 0; q < nseq; ++q) {
+                const SeqTemplate *p = tp[(size_t)q];
+                if (!p || t >= NTs[q]) continue;
+                const int a = part == 0 ? p->near_begin[t] : p->chunk_begin[t];
+                const int b = part == 0 ? p->chunk_begin[t] : p->near_begin[t + 1];
+                if (b > a) segs.push_back({p->tasks.data() + a, b - a, q, k});
+                k += (size_t)(b - a);
             }
         }
-        for (int s = 0; s < nseq; ++s) {
-            if (t >= NTs[s]) continue;
-            for (const Chunk &c : bucket[s][t]) out.push_back(make_int4(s, task_pack(c.type, c.I, c.J), c.Ka, c.Kb));
-        }
     }
+    auto copy = [&](size_t s0, size_t s1) {
+        for (size_t g = s0; g < s1; ++g) {
+            const Seg &sg = segs[g];
+            for (int e = 0; e < sg.count; ++e) {
+                int4 v = sg.src[e];
+                v.x = sg.seq;
+                out[sg.dst + (size_t)e] = v;
+            }
+        }
+    };
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int nth = total < (1u << 20) ? 1 : (int)std::max(1u, std::min(hw, 16u));
+    if (nth == 1) {
+        copy(0, segs.size());
+    } else {
+        // split the segments into nth ranges of about equal task counts
+        std::vector<std::thread> th;
+        size_t g = 0;
+        for (int w = 0; w < nth && g < segs.size(); ++w) {
+            const size_t want = total * (size_t)(w + 1) / (size_t)nth;
+            size_t e = g;
+            while (e < segs.size() && (w == nth - 1 || segs[e].dst < want)) ++e;
+            if (e > g) th.emplace_back(copy, g, e);
+            g = e;
+        }
+        if (g < segs.size()) copy(g, segs.size());
+        for (auto &x : th) x.join();
+    }
+    return total;
 }
 
 void build_schedule_steps(int NT, int kc, int strip, std::vector<int4> &out, std::vector<int> &step_begin) {
