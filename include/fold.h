@@ -271,6 +271,31 @@ int fold_serve_submit(fold_ctx *ctx, const char *seq, int32_t n, uint64_t *ticke
 int fold_serve_poll(fold_ctx *ctx, uint64_t ticket, int32_t *max_pairs, int16_t *D_out);
 int fold_serve_stop(fold_ctx *ctx);
 
+/* Builds now, on up to 16 host threads, the task lists the serving loop (and
+ * single folds) of this context use for every sequence length up to max_n:
+ * they depend only on the length and are otherwise built when a length is
+ * first seen, adding that time (up to about 10 ms at n = 8000) to the first
+ * request of each size.  Lists are kept for the life of the process (up to
+ * 512 MiB, least recently used dropped first).  FOLD_EINVAL if ctx is NULL or
+ * max_n is outside [0, 65535]. */
+int fold_serve_warm(fold_ctx *ctx, int32_t max_n);
+
+/* Counters of the serving loop since fold_serve_start (for monitoring and
+ * tuning).  A "slice" is one persistent launch over the in-flight set. */
+typedef struct fold_serve_stats {
+    uint64_t slices;        /* persistent launches so far */
+    uint64_t tasks;         /* tasks those launches ran */
+    uint64_t admitted;      /* requests admitted into the device arena */
+    uint64_t finished;      /* requests done or failed */
+    double gpu_ms;          /* device time of the slices (CUDA events around each launch) */
+    double slice_ms;        /* host wall time from a slice's first enqueue to its results on the host */
+    double prep_ms;         /* host time gathering slices' task lists and descriptors */
+    int32_t queued;         /* waiting for admission now */
+    int32_t inflight;       /* on the device now */
+} fold_serve_stats;
+/* FOLD_EINVAL if ctx or out is NULL or no serving loop runs. */
+int fold_serve_stats_get(fold_ctx *ctx, fold_serve_stats *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,9 @@
 // tasks in list order, so the kernel can always make progress.
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "fold_common.h"
@@ -35,25 +37,26 @@
 namespace fold {
 
 namespace {
-struct Chunk { int type, I, J, Ka, Kb; };
+struct Chunk { int type, I, J, Ka, Kb, step; };
 
-// Splits [lo, hi] into chunks whose sizes grow geometrically (1, 2, 4, ... up
-// to kc) from both ends toward the middle.  The blocks at either end of a
-// tile's middle range are the last to become ready (they need the most
-// recent tiles), so they come in small pieces that finish quickly; the middle
-// blocks, ready long before, form the big chunks.  Without `geometric` the
-// chunks are kc blocks each (batches: the folds' own critical paths matter
-// little there, the number of tasks does).
-std::vector<std::pair<int, int>> split_range(int lo, int hi, int kc, bool geometric) {
-    std::vector<std::pair<int, int>> head, tail;
+// Splits [lo, hi] into chunks (appended to `out`, which is cleared first) whose sizes grow
+// geometrically (1, 2, 4, ... up to kc) from both ends toward the middle.  The blocks at either
+// end of a tile's middle range are the last to become ready (they need the most recent tiles),
+// so they come in small pieces that finish quickly; the middle blocks, ready long before, form
+// the big chunks.  Without `geometric` the chunks are kc blocks each (batches: the folds' own
+// critical paths matter little there, the number of tasks does).
+void split_range(int lo, int hi, int kc, bool geometric, std::vector<std::pair<int, int>> &out,
+                 std::vector<std::pair<int, int>> &tail) {
+    out.clear();
+    tail.clear();
     if (!geometric) {
-        for (int a = lo; a <= hi; a += kc) head.push_back({a, std::min(hi, a + kc - 1)});
-        return head;
+        for (int a = lo; a <= hi; a += kc) out.push_back({a, std::min(hi, a + kc - 1)});
+        return;
     }
     int size = 1;
     while (lo <= hi) {
         const int a = std::min(size, hi - lo + 1);
-        head.push_back({lo, lo + a - 1});
+        out.push_back({lo, lo + a - 1});
         lo += a;
         if (lo > hi) break;
         const int b = std::min(size, hi - lo + 1);
@@ -61,80 +64,120 @@ std::vector<std::pair<int, int>> split_range(int lo, int hi, int kc, bool geomet
         hi -= b;
         size = std::min(2 * size, kc);
     }
-    head.insert(head.end(), tail.rbegin(), tail.rend());
-    return head;
-}
+    out.insert(out.end(), tail.rbegin(), tail.rend());
 }
 
-namespace {
-// The task list of one sequence with NT tiles per side (sequence index 0), step by step: the NEAR
-// tasks of tile diagonal t are tasks[near_begin[t], chunk_begin[t]), the chunks placed after
-// them tasks[chunk_begin[t], near_begin[t+1]).
-struct SeqTemplate {
-    std::vector<int4> tasks;
-    std::vector<int> near_begin, chunk_begin;
-};
-
+// The task list of one sequence (index 0), step by step.  Chunks are generated in order of
+// (tile diagonal J-I, row I), a tile's single-tile chunks before the strip chunks starting at it,
+// and then placed by a stable counting sort on their step: within a step the most urgent chunk
+// (lowest diagonal, then row) comes first.
 void build_one(int NT, int kc, int S, bool geometric, SeqTemplate &tp) {
-    std::vector<std::vector<Chunk>> bucket(NT > 0 ? NT : 1);
-    std::vector<int> nfar((size_t)NT * NT, 0);
-    auto place = [&](int d) { return d + 1; };
-    // single-tile chunks
+    tp.tasks.clear();
+    tp.near_begin.assign((size_t)NT + 1, 0);
+    tp.chunk_begin.assign((size_t)std::max(NT, 0), 0);
+    if (NT <= 0) return;
+    std::vector<int> nfar((size_t)NT * NT, 0), per_step((size_t)NT, 0);
+    std::vector<Chunk> chunks;
+    std::vector<std::pair<int, int>> parts, tail;
+    auto add = [&](int type, int I, int J, int Jl, int Ka, int Kb) {
+        // placed right after the NEAR tasks of the diagonal that follows the last tile it reads
+        // (and, past the P ring's depth, the tile whose P slot it reuses)
+        int d = std::max(Kb - I, Jl - Ka);
+        if (Jl - I >= kRing) d = std::max(d, Jl - I - kRing);
+        chunks.push_back({type, I, J, Ka, Kb, d + 1});
+        per_step[(size_t)d + 1]++;
+        for (int Jt = J; Jt <= Jl; ++Jt) nfar[(size_t)I * NT + Jt]++;
+    };
     for (int t = 4; t < NT; ++t) {
         for (int I = 0; I + t < NT; ++I) {
             const int J = I + t;
-            const int J0 = J / S * S;
-            const bool has_strip = S > 1 && J0 - 2 >= I + S + 1;
-            int ranges[2][2] = {{I + 2, J - 2}, {1, 0}};
-            if (has_strip) {
-                ranges[0][0] = I + 2; ranges[0][1] = I + S;
-                ranges[1][0] = J0 - 1; ranges[1][1] = J - 2;
+            // single-tile chunks: all middle blocks, or, where the tile is covered by a strip, the
+            // blocks next to its two ends
+            const int J0s = J / S * S;
+            if (S > 1 && J0s - 2 >= I + S + 1) {
+                split_range(I + 2, I + S, kc, geometric, parts, tail);
+                for (const auto &ck : parts) add(kTaskFar, I, J, J, ck.first, ck.second);
+                split_range(J0s - 1, J - 2, kc, geometric, parts, tail);
+                for (const auto &ck : parts) add(kTaskFar, I, J, J, ck.first, ck.second);
+            } else {
+                split_range(I + 2, J - 2, kc, geometric, parts, tail);
+                for (const auto &ck : parts) add(kTaskFar, I, J, J, ck.first, ck.second);
             }
-            for (auto &rg : ranges) {
-                for (const auto &ck : split_range(rg[0], rg[1], kc, geometric)) {
-                    const int Ka = ck.first, Kb = ck.second;
-                    int d = std::max(Kb - I, J - Ka);
-                    if (t >= kRing) d = std::max(d, t - kRing);
-                    bucket[place(d)].push_back({kTaskFar, I, J, Ka, Kb});
-                    nfar[(size_t)I * NT + J]++;
-                }
-            }
-        }
-    }
-    // strip chunks over tiles (I, J0..J0+Seff-1)
-    if (S > 1) {
-        for (int I = 0; I < NT; ++I) {
-            for (int J0 = (I + S + 3 + S - 1) / S * S; J0 < NT; J0 += S) {
-                const int Seff = std::min(S, NT - J0);
-                const int Jl = J0 + Seff - 1;
-                for (const auto &ck : split_range(I + S + 1, J0 - 2, kc, geometric)) {
-                    const int Ka = ck.first, Kb = ck.second;
-                    int d = std::max(Kb - I, Jl - Ka);
-                    if (Jl - I >= kRing) d = std::max(d, Jl - I - kRing);
-                    bucket[place(d)].push_back({kTaskFarStrip, I, J0, Ka, Kb});
-                    for (int J = J0; J <= Jl; ++J) nfar[(size_t)I * NT + J]++;
-                }
+            // strip chunks over tiles (I, J..J+Seff-1), for strip starts J >= I+S+3
+            if (S > 1 && J % S == 0 && J >= I + S + 3) {
+                const int Jl = std::min(J + S - 1, NT - 1);
+                split_range(I + S + 1, J - 2, kc, geometric, parts, tail);
+                for (const auto &ck : parts) add(kTaskFarStrip, I, J, Jl, ck.first, ck.second);
             }
         }
     }
-    // most urgent first: lower tile diagonal, then row
-    for (auto &bk : bucket)
-        std::stable_sort(bk.begin(), bk.end(), [](const Chunk &x, const Chunk &y) {
-            const int dx = x.J - x.I, dy = y.J - y.I;
-            return dx != dy ? dx < dy : x.I < y.I;
-        });
-    tp.near_begin.assign(NT + 1, 0);
-    tp.chunk_begin.assign(NT, 0);
+    // step t: NEAR tasks of tile diagonal t, then the chunks placed at t
+    std::vector<size_t> slot((size_t)NT);
+    size_t k = 0;
     for (int t = 0; t < NT; ++t) {
-        tp.near_begin[t] = (int)tp.tasks.size();
-        for (int I = 0; I + t < NT; ++I)
-            tp.tasks.push_back(make_int4(0, task_pack(kTaskNear, I, I + t), nfar[(size_t)I * NT + I + t], 0));
-        tp.chunk_begin[t] = (int)tp.tasks.size();
-        for (const Chunk &ck : bucket[t]) tp.tasks.push_back(make_int4(0, task_pack(ck.type, ck.I, ck.J), ck.Ka, ck.Kb));
+        tp.near_begin[(size_t)t] = (int)k;
+        k += (size_t)(NT - t);
+        tp.chunk_begin[(size_t)t] = (int)k;
+        slot[(size_t)t] = k;
+        k += (size_t)per_step[(size_t)t];
     }
-    tp.near_begin[NT] = (int)tp.tasks.size();
+    tp.near_begin[(size_t)NT] = (int)k;
+    tp.tasks.resize(k);
+    for (int t = 0; t < NT; ++t) {
+        int4 *o = tp.tasks.data() + tp.near_begin[(size_t)t];
+        for (int I = 0; I + t < NT; ++I) o[I] = make_int4(0, task_pack(kTaskNear, I, I + t), nfar[(size_t)I * NT + I + t], 0);
+    }
+    for (const Chunk &ck : chunks)
+        tp.tasks[slot[(size_t)ck.step]++] = make_int4(0, task_pack(ck.type, ck.I, ck.J), ck.Ka, ck.Kb);
 }
+
+// Templates are kept for the life of the process (they depend only on the sizes), up to
+// kTemplateCacheBytes of tasks; past that the least recently used ones no caller holds are
+// dropped.
+constexpr size_t kTemplateCacheBytes = size_t(512) << 20;
+struct TemplateCache {
+    std::mutex mu;
+    std::map<std::tuple<int, int, int, bool>, std::pair<std::shared_ptr<const SeqTemplate>, unsigned long long>> m;
+    size_t bytes = 0;
+    unsigned long long clock = 0;
+};
+TemplateCache &template_cache() {
+    static TemplateCache *c = new TemplateCache();   // never destroyed: used from threads that may outlive statics
+    return *c;
+}
+size_t template_bytes(const SeqTemplate &t) { return t.tasks.size() * sizeof(int4); }
 }  // namespace
+
+std::shared_ptr<const SeqTemplate> seq_template(int NT, int kc, int strip, bool geometric) {
+    if (kc < 1) kc = 1;
+    if (strip < 1) strip = 1;
+    const auto key = std::make_tuple(NT, kc, strip, geometric);
+    TemplateCache &c = template_cache();
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        auto it = c.m.find(key);
+        if (it != c.m.end()) {
+            it->second.second = ++c.clock;
+            return it->second.first;
+        }
+    }
+    auto tp = std::make_shared<SeqTemplate>();
+    build_one(NT, kc, strip, geometric, *tp);
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto ins = c.m.emplace(key, std::make_pair(std::shared_ptr<const SeqTemplate>(tp), ++c.clock));
+    if (!ins.second) return ins.first->second.first;   // another thread built it meanwhile
+    c.bytes += template_bytes(*tp);
+    while (c.bytes > kTemplateCacheBytes) {
+        auto victim = c.m.end();
+        for (auto it = c.m.begin(); it != c.m.end(); ++it)
+            if (it->second.first.use_count() == 1 && (victim == c.m.end() || it->second.second < victim->second.second))
+                victim = it;
+        if (victim == c.m.end()) break;
+        c.bytes -= template_bytes(*victim->second.first);
+        c.m.erase(victim);
+    }
+    return ins.first->second.first;
+}
 
 void build_schedule(const std::vector<int> &NTs, int kc, int strip, std::vector<int4> &out, bool geometric) {
     out.clear();
@@ -146,16 +189,14 @@ size_t build_schedule_into(const std::vector<int> &NTs, int kc, int strip, bool 
     const int nseq = (int)NTs.size();
     int maxNT = 0;
     for (int v : NTs) maxNT = std::max(maxNT, v);
-    if (kc < 1) kc = 1;
-    if (strip < 1) strip = 1;
     // one template per distinct size (a batch has few), then every sequence's copy interleaved:
     // for each step t, the NEAR tasks of all sequences, then their chunks
-    std::map<int, SeqTemplate> tpl;
+    std::map<int, std::shared_ptr<const SeqTemplate>> tpl;
     for (int v : NTs)
-        if (v > 0 && !tpl.count(v)) build_one(v, kc, strip, geometric, tpl[v]);
+        if (v > 0 && !tpl.count(v)) tpl[v] = seq_template(v, kc, strip, geometric);
     std::vector<const SeqTemplate *> tp((size_t)nseq, nullptr);
     for (int q = 0; q < nseq; ++q)
-        if (NTs[q] > 0) tp[(size_t)q] = &tpl[NTs[q]];
+        if (NTs[q] > 0) tp[(size_t)q] = tpl[NTs[q]].get();
     size_t total = 0;
     for (int q = 0; q < nseq; ++q)
         if (tp[(size_t)q]) total += tp[(size_t)q]->tasks.size();
@@ -210,21 +251,6 @@ size_t build_schedule_into(const std::vector<int> &NTs, int kc, int strip, bool 
         for (auto &x : th) x.join();
     }
     return total;
-}
-
-void build_schedule_steps(int NT, int kc, int strip, std::vector<int4> &out, std::vector<int> &step_begin) {
-    std::vector<int> nts(1, NT);
-    build_schedule(nts, kc, strip, out);
-    // tasks are emitted step by step: NEAR tasks of diagonal t, then the chunks placed at t
-    step_begin.assign(NT + 1, (int)out.size());
-    int t = -1;
-    for (int k = 0; k < (int)out.size(); ++k) {
-        if (task_type(out[k].y) == kTaskNear) {
-            int d = task_J(out[k].y) - task_I(out[k].y);
-            while (t < d) step_begin[++t] = k;
-        }
-    }
-    step_begin[NT] = (int)out.size();
 }
 
 // Independent check of a single-sequence list: every middle block K of every

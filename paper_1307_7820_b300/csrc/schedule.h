@@ -2,6 +2,7 @@
 #pragma once
 #include <stddef.h>
 
+#include <memory>
 #include <vector>
 #include <vector_types.h>
 
@@ -15,10 +16,15 @@ void build_schedule(const std::vector<int> &NTs, int kc, int strip, std::vector<
 // The same list written to out[0, total) when cap >= total; returns total (out may be null to count).
 size_t build_schedule_into(const std::vector<int> &NTs, int kc, int strip, bool geometric, int4 *out, size_t cap);
 
-// Same list for one sequence, with step_begin[t] = index of the first task of
-// step t (the NEAR tasks of tile diagonal t and the chunks placed after them);
-// step_begin[NT] = out.size().
-void build_schedule_steps(int NT, int kc, int strip, std::vector<int4> &out, std::vector<int> &step_begin);
+// The list of one sequence with NT tiles per side (sequence index 0 in every task), step by
+// step: step t is tasks[near_begin[t], near_begin[t+1]), the NEAR tasks of tile diagonal t in
+// [near_begin[t], chunk_begin[t]) and the chunks placed after them in the rest.
+struct SeqTemplate {
+    std::vector<int4> tasks;
+    std::vector<int> near_begin, chunk_begin;
+};
+// Built once per (NT, kc, strip, geometric) and shared (process-wide, thread-safe cache).
+std::shared_ptr<const SeqTemplate> seq_template(int NT, int kc, int strip, bool geometric);
 
 // Checks a single-sequence list (coverage, chunk counts, dependency order); 0 = valid.
 int check_schedule(int NT, int kc, int strip, const std::vector<int4> &tasks);

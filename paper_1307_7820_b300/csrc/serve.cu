@@ -15,10 +15,12 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -36,6 +38,7 @@ constexpr int kSliceMin = 2;         // tile diagonals per request per launch: a
 constexpr int kSliceMax = 64;        // launch takes about kSliceTargetMs
 constexpr double kSliceTargetMs = 2.0;
 constexpr size_t kMaxQueued = 1 << 20;
+constexpr size_t kLaunchBytes0 = size_t(16) << 20;   // initial launch-list buffers (host and device)
 
 struct Request {
     uint64_t ticket = 0;
@@ -45,8 +48,7 @@ struct Request {
     Plan pl;
     size_t block = 0;                // arena byte offset
     size_t bytes = 0;
-    std::vector<int4> tasks;
-    std::vector<int> step_begin;
+    std::shared_ptr<const SeqTemplate> sched;   // task list of a fold of this size, by step (shared)
     int cursor = 0;                  // next tile diagonal to schedule
     int state = 0;                   // 0 queued, 1 in flight, 2 done, 3 failed
     int status = FOLD_OK;
@@ -108,10 +110,15 @@ struct ServeState {
     // launch buffers
     DevBuf d_launch;                 // control | results | SeqDesc | tasks
     HostBuf h_launch;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     unsigned long long launches = 0;
+    fold_serve_stats stats{};        // guarded by mu
 };
 
 static size_t al256(size_t v) { return (v + 255) / 256 * 256; }
+// capacity to ask for when `want` bytes are needed: at least double the current one, so that
+// growing launch lists reallocate (and synchronise) only a few times
+static size_t grown(size_t have, size_t want) { return want <= have ? have : std::max(want, 2 * have); }
 
 // SeqDesc of a request whose plan sits at arena byte offset `block`; every
 // pool pointer of the launch is the arena base, so offsets are in elements.
@@ -137,6 +144,7 @@ static void fail_inflight(ServeState *S, int status) {
         if (it == S->reqs.end()) continue;
         it->second.state = 3;
         it->second.status = status;
+        S->stats.finished++;
     }
     S->inflight.clear();
 }
@@ -168,6 +176,7 @@ static void serve_loop(ServeState *S) {
             for (uint64_t t : S->inflight) active.push_back(&S->reqs[t]);
         }
         if (active.empty()) continue;
+        const auto t_prep = std::chrono::steady_clock::now();
         // new requests: zeroed control/flag region and padded codes
         cudaError_t e = cudaSuccess;
         for (uint64_t t : admitted) {
@@ -182,40 +191,52 @@ static void serve_loop(ServeState *S) {
                 e = cudaMemcpyAsync(base + r->pl.off_codes, r->codes.data(), r->codes.size(), cudaMemcpyHostToDevice, S->st);
             // the host copy of the codes must stay alive until this copy ran: synchronised below
         }
-        // one slice: kSlice steps of every active request, interleaved step by step
-        std::vector<SeqDesc> sds(active.size());
-        std::vector<int4> tasks;
-        for (size_t k = 0; k < active.size(); ++k) sds[k] = arena_desc(*active[k], (int)k);
-        for (int off = 0; off < slice; ++off) {
-            for (size_t k = 0; k < active.size(); ++k) {
-                const Request &r = *active[k];
-                const int step = r.cursor + off;
-                if (step >= r.NT) continue;
-                for (int q = r.step_begin[step]; q < r.step_begin[step + 1]; ++q) {
-                    int4 tk = r.tasks[q];
-                    tk.x = (int)k;
-                    tasks.push_back(tk);
-                }
-            }
-        }
+        // one slice: `slice` steps of every active request, interleaved step by step, gathered
+        // straight into the pinned staging buffer (whole steps are contiguous in a template)
         const size_t cnt = active.size();
+        size_t ntasks = 0;
+        for (const Request *r : active) {
+            const int lo = std::min(r->cursor, r->NT), hi = std::min(r->cursor + slice, r->NT);
+            ntasks += (size_t)(r->sched->near_begin[hi] - r->sched->near_begin[lo]);
+        }
         const size_t o_res = 256, o_sd = al256(o_res + 4 * cnt), o_tasks = al256(o_sd + sizeof(SeqDesc) * cnt);
-        const size_t o_out = al256(o_tasks + sizeof(int4) * tasks.size());
+        const size_t o_out = al256(o_tasks + sizeof(int4) * ntasks);
         const size_t total = al256(o_out + 4 * cnt);
-        if (ensure_buf(S->d_launch, total) || ensure_host(S->h_launch, total)) {
+        if (ensure_buf(S->d_launch, grown(S->d_launch.bytes, total)) ||
+            ensure_host(S->h_launch, grown(S->h_launch.bytes, total))) {
             fail_inflight(S, FOLD_ENOMEM);
             continue;
         }
         uint8_t *h = reinterpret_cast<uint8_t *>(S->h_launch.ptr);
         uint8_t *d = reinterpret_cast<uint8_t *>(S->d_launch.ptr);
-        memcpy(h + o_sd, sds.data(), sizeof(SeqDesc) * cnt);
-        if (!tasks.empty()) memcpy(h + o_tasks, tasks.data(), sizeof(int4) * tasks.size());
+        SeqDesc *hsd = reinterpret_cast<SeqDesc *>(h + o_sd);
+        for (size_t k = 0; k < cnt; ++k) hsd[k] = arena_desc(*active[k], (int)k);
+        int4 *dst = reinterpret_cast<int4 *>(h + o_tasks);
+        for (int off = 0; off < slice; ++off) {
+            for (size_t k = 0; k < cnt; ++k) {
+                const Request &r = *active[k];
+                const int step = r.cursor + off;
+                if (step >= r.NT) continue;
+                const SeqTemplate &sc = *r.sched;
+                const int a = sc.near_begin[step], b = sc.near_begin[step + 1];
+                if (k == 0) {   // templates carry sequence index 0
+                    memcpy(dst, sc.tasks.data() + a, sizeof(int4) * (size_t)(b - a));
+                } else {
+                    for (int q = a; q < b; ++q) {
+                        int4 tk = sc.tasks[q];
+                        tk.x = (int)k;
+                        dst[q - a] = tk;
+                    }
+                }
+                dst += b - a;
+            }
+        }
         if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, o_sd, S->st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d + o_sd, h + o_sd, o_out - o_sd, cudaMemcpyHostToDevice, S->st);
         FoldParams p;
         memset(&p, 0, sizeof p);
         p.tasks = reinterpret_cast<const int4 *>(d + o_tasks);
-        p.ntasks = (int)tasks.size();
+        p.ntasks = (int)ntasks;
         p.queue_head = reinterpret_cast<int *>(d);
         p.error = reinterpret_cast<int *>(d) + 1;
         p.queue_head_far = reinterpret_cast<int *>(d) + 2;
@@ -236,13 +257,18 @@ static void serve_loop(ServeState *S) {
         p.timeout_ns = ctx->timeout_ms * 1000000LL;
         p.trace = nullptr;
         const auto t_launch = std::chrono::steady_clock::now();
+        if (e == cudaSuccess) e = cudaEventRecord(S->ev0, S->st);
         if (e == cudaSuccess && p.ntasks > 0) e = launch_fold(p, ctx->q, ctx->method, grid_for(ctx), S->st);
         if (e == cudaSuccess)
             e = launch_finalize(p.error, p.results, (int)cnt, reinterpret_cast<int32_t *>(d + o_out), S->st);
+        if (e == cudaSuccess) e = cudaEventRecord(S->ev1, S->st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h + o_out, d + o_out, 4 * cnt, cudaMemcpyDeviceToHost, S->st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
         S->launches += 3;
-        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_launch).count();
+        const auto t_done = std::chrono::steady_clock::now();
+        const double ms = std::chrono::duration<double, std::milli>(t_done - t_launch).count();
+        float gpu_ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&gpu_ms, S->ev0, S->ev1);
         const int used = slice;
         slice = std::max(kSliceMin, std::min(kSliceMax, (int)(slice * kSliceTargetMs / std::max(ms, 0.05))));
         if (e != cudaSuccess) {
@@ -252,10 +278,17 @@ static void serve_loop(ServeState *S) {
         }
         const int32_t *hres = reinterpret_cast<const int32_t *>(h + o_out);
         std::lock_guard<std::mutex> lk(S->mu);
+        S->stats.slices++;
+        S->stats.tasks += (uint64_t)p.ntasks;
+        S->stats.admitted += admitted.size();
+        S->stats.gpu_ms += gpu_ms;
+        S->stats.slice_ms += std::chrono::duration<double, std::milli>(t_done - t_prep).count();
+        S->stats.prep_ms += std::chrono::duration<double, std::milli>(t_launch - t_prep).count();
         std::vector<uint64_t> still;
         for (size_t k = 0; k < cnt; ++k) {
             Request &r = *active[k];
             if (hres[k] < 0) {   // a bounded device-side wait expired in this launch
+                S->stats.finished++;
                 r.state = 3;
                 r.status = -hres[k] == FOLD_ETIMEOUT ? FOLD_ETIMEOUT : FOLD_ECUDA;
                 continue;
@@ -264,6 +297,7 @@ static void serve_loop(ServeState *S) {
             if (r.cursor >= r.NT) {
                 r.state = 2;
                 r.result = r.n >= 2 ? hres[k] : 0;
+                S->stats.finished++;
             } else {
                 still.push_back(r.ticket);
             }
@@ -293,10 +327,26 @@ int fold_serve_start(fold_ctx *ctx, int64_t budget_bytes, int32_t max_inflight) 
     }
     S->arena.init(S->budget);
     if (cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&S->poll_st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&S->poll_st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&S->ev0) != cudaSuccess || cudaEventCreate(&S->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        if (S->ev0) cudaEventDestroy(S->ev0);
+        if (S->st) cudaStreamDestroy(S->st);
+        if (S->poll_st) cudaStreamDestroy(S->poll_st);
         cudaFree(S->arena_base);
         delete S;
         return FOLD_ECUDA;
+    }
+    // launch lists of up to about a million tasks without reallocating (a reallocation synchronises)
+    if (ensure_buf(S->d_launch, kLaunchBytes0) || ensure_host(S->h_launch, kLaunchBytes0)) {
+        if (S->d_launch.ptr) cudaFree(S->d_launch.ptr);
+        cudaEventDestroy(S->ev0);
+        cudaEventDestroy(S->ev1);
+        cudaStreamDestroy(S->st);
+        cudaStreamDestroy(S->poll_st);
+        cudaFree(S->arena_base);
+        delete S;
+        return FOLD_ENOMEM;
     }
     ctx->serve = S;
     S->th = std::thread(serve_loop, S);
@@ -317,8 +367,8 @@ int fold_serve_submit(fold_ctx *ctx, const char *seq, int32_t n, uint64_t *ticke
     r.codes.assign((size_t)std::max(Np, 1), (uint8_t)kPadCode);
     if (!encode_seq(seq, n, r.codes.data())) return FOLD_EINVAL;
     if (n > 0) {
-        int kc = ctx->kc_override > 0 ? ctx->kc_override : kc_auto(r.NT);
-        build_schedule_steps(r.NT, kc, strip_of(ctx->q, ctx->method), r.tasks, r.step_begin);
+        const int kc = ctx->kc_override > 0 ? ctx->kc_override : kc_auto(r.NT);
+        r.sched = seq_template(r.NT, kc, strip_of(ctx->q, ctx->method), true);
     }
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->reqs.size() >= kMaxQueued) return FOLD_EAGAIN;
@@ -373,6 +423,36 @@ int fold_serve_poll(fold_ctx *ctx, uint64_t ticket, int32_t *max_pairs, int16_t 
     return status;
 }
 
+int fold_serve_warm(fold_ctx *ctx, int32_t max_n) {
+    if (!ctx || max_n < 0 || max_n > FOLD_MAX_N) return FOLD_EINVAL;
+    if (max_n == 0) return FOLD_OK;
+    int n = max_n;
+    const int NTmax = make_plan(&n, 1, ctx->q, ctx->method).NTs[0];
+    const int strip = strip_of(ctx->q, ctx->method), kco = ctx->kc_override;
+    // largest first, so the threads finish together
+    std::atomic<int> next(NTmax);
+    auto work = [&] {
+        for (int NT; (NT = next.fetch_sub(1)) >= 1;) seq_template(NT, kco > 0 ? kco : kc_auto(NT), strip, true);
+    };
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int nth = (int)std::max(1u, std::min(hw, 16u));
+    std::vector<std::thread> th;
+    for (int k = 1; k < nth; ++k) th.emplace_back(work);
+    work();
+    for (auto &x : th) x.join();
+    return FOLD_OK;
+}
+
+int fold_serve_stats_get(fold_ctx *ctx, fold_serve_stats *out) {
+    if (!ctx || !out || !ctx->serve) return FOLD_EINVAL;
+    ServeState *S = ctx->serve;
+    std::lock_guard<std::mutex> lk(S->mu);
+    *out = S->stats;
+    out->queued = (int32_t)S->queued.size();
+    out->inflight = (int32_t)S->inflight.size();
+    return FOLD_OK;
+}
+
 int fold_serve_stop(fold_ctx *ctx) {
     if (!ctx) return FOLD_EINVAL;
     ServeState *S = ctx->serve;
@@ -392,6 +472,8 @@ int fold_serve_stop(fold_ctx *ctx) {
     cudaFree(S->arena_base);
     cudaStreamDestroy(S->st);
     cudaStreamDestroy(S->poll_st);
+    cudaEventDestroy(S->ev0);
+    cudaEventDestroy(S->ev1);
     delete S;
     ctx->serve = nullptr;
     return FOLD_OK;

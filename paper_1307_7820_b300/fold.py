@@ -31,7 +31,9 @@ FOLD_STATIC_MAX_N = 1024
 ABI_SYMBOLS = (
     "fold_init", "fold_destroy", "fold_strerror", "fold_set_option", "fold_get_option", "fold_rtable",
     "fold_score", "fold_workspace_bytes", "fold_score_dev", "fold_batch",
-    "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop", "fold_trace_copy",
+    "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop", "fold_serve_stats_get",
+    "fold_serve_warm",
+    "fold_trace_copy",
     "fold_score_static", "fold_schedule_check", "fold_tune", "fold_tune_q", "fold_tune_save", "fold_tune_load",
     "fold_structure", "fold_structure_workspace_bytes", "fold_structure_dev",
 )
@@ -50,6 +52,16 @@ class TuneResult(ctypes.Structure):
     """struct fold_tune_result"""
     _fields_ = [("q", ctypes.c_int32), ("near_ctas", ctypes.c_int32), ("columns", ctypes.c_int32),
                 ("kchunk", ctypes.c_int32), ("ms", ctypes.c_float), ("default_ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServeStats(ctypes.Structure):
+    """struct fold_serve_stats"""
+    _fields_ = [("slices", ctypes.c_uint64), ("tasks", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
+                ("finished", ctypes.c_uint64), ("gpu_ms", ctypes.c_double), ("slice_ms", ctypes.c_double),
+                ("prep_ms", ctypes.c_double), ("queued", ctypes.c_int32), ("inflight", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -93,6 +105,8 @@ def lib():
     L.fold_serve_submit.argtypes = [vp, ctypes.c_char_p, i32, P(ctypes.c_uint64)]
     L.fold_serve_poll.argtypes = [vp, ctypes.c_uint64, P(i32), vp]
     L.fold_serve_stop.argtypes = [vp]
+    L.fold_serve_stats_get.argtypes = [vp, P(ServeStats)]
+    L.fold_serve_warm.argtypes = [vp, i32]
     L.fold_trace_copy.argtypes = [vp, vp, i64]
     L.fold_score_static.argtypes = [vp, i32, u16, vp, vp, vp]
     L.fold_score_static.restype = ctypes.c_int
@@ -288,6 +302,18 @@ def fold_serve_poll(ctx: int, ticket: int, D_out: np.ndarray | None = None):
 
 def fold_serve_stop(ctx: int) -> None:
     _check(lib().fold_serve_stop(ctx), "fold_serve_stop")
+
+
+def fold_serve_warm(ctx: int, max_n: int) -> None:
+    """Build the task lists for every length up to max_n now instead of at first use."""
+    _check(lib().fold_serve_warm(ctx, max_n), "fold_serve_warm")
+
+
+def fold_serve_stats(ctx: int) -> dict:
+    """Counters of the running serving loop (slices, tasks, requests, device and host time)."""
+    st = ServeStats()
+    _check(lib().fold_serve_stats_get(ctx, ctypes.byref(st)), "fold_serve_stats_get")
+    return st.as_dict()
 
 
 # ---------------------------------------------------------------- convenience

@@ -60,6 +60,9 @@ def test_null_and_range_arguments(L):
     assert L.fold_tune_q(0, 0x5A48, 0, lens, 0, 8, 8, ctypes.byref(r)) == fold.FOLD_EINVAL   # no lengths
     assert L.fold_tune_save(None, b"/tmp/x") == fold.FOLD_EINVAL
     assert L.fold_tune_load(None, b"/tmp/x") == fold.FOLD_EINVAL
+    st = fold.ServeStats()
+    assert L.fold_serve_stats_get(None, ctypes.byref(st)) == fold.FOLD_EINVAL
+    assert L.fold_serve_warm(None, 100) == fold.FOLD_EINVAL
 
 
 def test_pair_mask_constants():

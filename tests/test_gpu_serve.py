@@ -47,6 +47,12 @@ def test_serve_mix_equals_alone():
         got = [res[t] for t in tickets]
         assert got == alone
         assert got == [oracle.score(s) if len(s) else 0 for s in seqs]
+        st = fold.fold_serve_stats(f.ctx)
+        nonempty = sum(1 for s in seqs if len(s))
+        assert st["admitted"] == st["finished"] == nonempty
+        assert st["queued"] == 0 and st["inflight"] == 0
+        assert st["slices"] >= 1 and st["tasks"] >= nonempty
+        assert 0 < st["gpu_ms"] <= st["slice_ms"] and st["prep_ms"] >= 0
     finally:
         fold.fold_serve_stop(f.ctx)
         f.close()
@@ -88,6 +94,26 @@ def test_serve_poll_unknown_ticket_and_restart():
         fold.fold_serve_start(f.ctx, 1 << 28, 4)
         t = fold.fold_serve_submit(f.ctx, "ACUGACUG")
         assert _drain(f.ctx, [t])[t] == 3
+    finally:
+        fold.fold_serve_stop(f.ctx)
+        f.close()
+
+
+def test_serve_warm_then_mixed_lengths():
+    """Task lists built ahead (for every length up to 3000) give the same results as lists built
+    at first use; lengths past the warmed range still work."""
+    f = fold.Folder(q=8)
+    try:
+        with pytest.raises(fold.FoldError) as ei:
+            fold.fold_serve_warm(f.ctx, -1)
+        assert ei.value.code == fold.FOLD_EINVAL
+        fold.fold_serve_warm(f.ctx, 3000)
+        fold.fold_serve_start(f.ctx, 4 << 30, 32)
+        lens = [40, 999, 2048, 3000, 3100, 17, 1500]
+        seqs = [synth.variant(["uniform", "gc_rich", "structured"][k % 3], L, 4200 + k) for k, L in enumerate(lens)]
+        tickets = [fold.fold_serve_submit(f.ctx, s) for s in seqs]
+        res = _drain(f.ctx, tickets)
+        assert [res[t] for t in tickets] == [oracle.score(s) for s in seqs]
     finally:
         fold.fold_serve_stop(f.ctx)
         f.close()
