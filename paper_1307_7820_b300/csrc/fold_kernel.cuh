@@ -147,6 +147,10 @@ struct Cfg {
     static constexpr int RBYTES = (M == kPlain) ? 0 : (NIB ? (1 << (2 * NB - 1)) : (1 << (2 * NB)));
 };
 
+// two-vector: residual splits per row of a tile (the window of rows below it)
+template <int Q>
+constexpr int NW_RES = Q > 1 ? Q - 1 : 1;
+
 // per-warp shared scratch
 template <int Q, int M>
 struct __align__(16) WarpScratch {
@@ -157,6 +161,9 @@ struct __align__(16) WarpScratch {
     static constexpr int LF = PL ? 1 : T;          // two-vector: late-block row features
     static constexpr int SS = strip_of(Q, M);
     static constexpr int DS = PL ? 40 : 32;    // diagonal-tile row stride: 16-byte rows (uint4 / cp.async)
+    static constexpr int NWP = (Q > 2 ? Q : 2) / 2;   // two-vector residual window: Q-1 values in pairs
+    static constexpr int NWPA = (NWP + 3) / 4 * 4;     // ... padded to 16-byte rows
+    static constexpr int GA = (G + 3) / 4 * 4;         // groups padded to 16-byte rows
     union {
         struct {                       // chunk tasks
             int2 rf[G][32];            // FAR staging (two-vector): (A, h-row byte offset)
@@ -173,10 +180,15 @@ struct __align__(16) WarpScratch {
     alignas(16) int16_t lrow[2][LR][32];  // NEAR late blocks (plain): rows of tiles (I,J-1), (I,I+1)
     alignas(16) uint32_t colpk[PL ? 16 : 1][32];  // NEAR (plain): (D(IT+2m+1,j), D(IT+2m+2,j)) pairs, per lane
     alignas(16) uint32_t lrf[2][LF][G];  // NEAR late blocks (two-vector): row features of (I,J-1), (I,I+1)
-    uint32_t cbc[G + 1][32];           // NEAR (two-vector): (base << 16 | bits) of the lane's column groups;
-                                       // row G takes the stores of rows that complete no group
+    alignas(16) uint32_t cbc[32][PL ? 4 : GA];  // NEAR (two-vector): (B << 16 | bits) of the lane's column
+                                       // groups, lane-major (one 16-byte load per four groups)
     alignas(16) int16_t diag[T][DS];   // diagonal tile (I,I) rows
-    alignas(16) uint32_t drf[T][G];    // diagonal tile row features
+    alignas(16) uint32_t gw[PL ? 1 : T][PL ? 4 : GA];  // NEAR (two-vector): per row of the diagonal tile
+                                       // and group, (A << 16) | R-row offset (h for nibble tables), with
+                                       // A = -32768 for groups not complete below that row
+    alignas(16) uint32_t rpk[PL ? 1 : T][PL ? 4 : NWPA];  // NEAR (two-vector): per row, the residual
+                                       // splits' D(i, k-1) as int16 pairs, -32768 where k is not a
+                                       // residual split of the row
     int16_t pm[T][32];                 // far partial max of each row (lane = column)
     alignas(16) int16_t y[2][32];      // closure exchange, double-buffered (read back as uint4)
     int16_t left[T + 2];               // D(IT+m, JT-1)
@@ -194,6 +206,8 @@ struct ScratchChecks {
     static_assert(offsetof(WS, rows) % 16 == 0, "rows must be 16-byte aligned");
     static_assert(offsetof(WS, lrow) % 16 == 0, "lrow must be 16-byte aligned");
     static_assert(offsetof(WS, lrf) % 16 == 0, "lrf must be 16-byte aligned");
+    static_assert(offsetof(WS, cbc) % 16 == 0 && offsetof(WS, gw) % 16 == 0 && offsetof(WS, rpk) % 16 == 0,
+                  "cbc, gw and rpk rows are read as uint4");
     static_assert(offsetof(WS, diag) % 16 == 0 && (WS::DS * 2) % 16 == 0, "diag rows 16-byte aligned");
     static_assert(sizeof(WarpScratch<Q, M>) % 16 == 0, "scratch stride must keep 16-byte alignment");
     static constexpr bool ok = true;
@@ -221,6 +235,24 @@ template <int Q>
 __device__ __forceinline__ int hrow_offset(int h) {
     if constexpr (Q >= 10) return h << (Q - 2);   // nibbles: 2^(q-1) entries = 2^(q-2) bytes per row
     else return h << (Q - 1);
+}
+
+// One full group's candidate of Eq. 3, A + B + R[h][c], scaled by 2^16 (the low half is not zero):
+// w = (A << 16) | R-row offset of h (h itself for nibble tables), cb = (B << 16) | c.  A and B are
+// D values of two disjoint pieces of [i, j], so A + B <= (j-i+1)/2 < 2^15 and one 32-bit add gives
+// A + B in the high half (also for A = -32768, which stays negative with B >= 0) and the R index in
+// the low half (the offset and c share no bits).  Candidates compare as signed integers.
+template <int Q>
+__device__ __forceinline__ int group_term(const uint8_t *Rs, uint32_t w, uint32_t cb) {
+    if constexpr (Q >= 10) {
+        constexpr unsigned BM = (1u << (Q - 1)) - 1;
+        const uint32_t s = w + (cb & 0xffff0000u);
+        const int v = rlookup<Q>(Rs, hrow_offset<Q>((int)(w & BM)), (int)(cb & BM));
+        return (int)(s + ((uint32_t)v << 16));
+    } else {
+        const uint32_t s = w + cb;
+        return (int)(s + ((uint32_t)Rs[s & 0xffffu] << 16));
+    }
 }
 
 // ---------------------------------------------------------------- far blocks
@@ -640,7 +672,6 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     const int pbp = (cs.k - 1) & 1;   // buffer of the producer's tile (I, J-1)
     // old-tile inputs: diagonal tile rows and features, late block K = I+1 rows
     auto &dg = ws.diag;
-    auto &drf = ws.drf;
     auto &lrf1 = ws.lrf[1];
     auto &lrow1 = ws.lrow[1];
     if constexpr (COL) cs.failed = true;   // cleared when the tile completes
@@ -734,8 +765,13 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             for (int e = 0; e < E; ++e) {
                 const int idx = e * 32 + lane;
                 if (idx < T * G) {
-                    drf[idx / G][idx % G] = fv[e];
-                    lrf1[idx / G][idx % G] = fb[e];
+                    // the row's word for group gl: A, or -32768 while the group is not complete
+                    // below the row (gl*q <= row), and the R-row offset of h
+                    const int rw = idx / G, gl = idx % G;
+                    const uint32_t hw = C::NIB ? (fv[e] & C::BMASK) : (uint32_t)hrow_offset<Q>((int)(fv[e] & C::BMASK));
+                    const uint32_t aw = (gl * Q > rw) ? (fv[e] & 0xffff0000u) : 0x80000000u;
+                    ws.gw[rw][gl] = aw | hw;
+                    lrf1[rw][gl] = fb[e];
                 }
             }
         } else {
@@ -818,11 +854,16 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll
             for (int gl = 0; gl < G; ++gl) {
                 // column mode: the features of block I+1 are this warp's previous tile's
-                const uint32_t cf = COL ? ws.cbc[gl][c] : __ldcg(CF + (size_t)((I + 1) * G + gl) * Np + j);
+                const uint32_t cf = COL ? ws.cbc[c][gl] : __ldcg(CF + (size_t)((I + 1) * G + gl) * Np + j);
                 lB[1][gl] = (int)(cf >> 16);
                 lC[1][gl] = (int)(cf & C::BMASK);
             }
         }
+        // this tile's column groups start as (B, c) = (0, 0): a group that is not complete below a
+        // row then adds at most -32768 + q - 1 there (its A is -32768)
+#pragma unroll
+        for (int g4 = 0; g4 < WarpScratch<Q, M>::GA / 4; ++g4)
+            reinterpret_cast<uint4 *>(&ws.cbc[c][0])[g4] = make_uint4(0u, 0u, 0u, 0u);
     } else {
         if (COL && prod) {
             const int16_t(*pt)[33] = pbp ? prod->tile1 : prod->tile;
@@ -883,6 +924,28 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         for (int v = 0; v < 4; ++v) dst[v] = ra[v];
     }
     __syncwarp();
+    if constexpr (TV) {
+        // per row of the diagonal tile (lane = row), the residual splits' D(i, k-1) in int16 pairs:
+        // slot e holds k = i+2+e while k is at most the end ce of the first group that starts after
+        // the row, -32768 otherwise (the groups from ce on are full groups of the row)
+        using WS = WarpScratch<Q, M>;
+        if (t >= 1 && lane < T) {
+            const int rr = lane;
+            const int ce = (rr / Q + 1) * Q;
+            uint32_t w[WS::NWPA];
+#pragma unroll
+            for (int k = 0; k < WS::NWPA; ++k) w[k] = 0x80008000u;
+#pragma unroll
+            for (int e = 0; e < NW_RES<Q>; ++e) {
+                const int kk = rr + 2 + e;
+                const uint32_t v = (kk <= ce) ? (uint32_t)(uint16_t)dg[rr][min(kk, T) - 1] : 0x8000u;
+                w[e >> 1] = (e & 1) ? ((w[e >> 1] & 0xffffu) | (v << 16)) : ((w[e >> 1] & 0xffff0000u) | v);
+            }
+#pragma unroll
+            for (int k4 = 0; k4 < WS::NWPA / 4; ++k4)
+                reinterpret_cast<uint4 *>(&ws.rpk[rr][0])[k4] = make_uint4(w[4 * k4], w[4 * k4 + 1], w[4 * k4 + 2], w[4 * k4 + 3]);
+        }
+    }
     // the two late middle blocks for every row at once (independent lookups, high ILP)
     if constexpr (TV) {
 #pragma unroll
@@ -956,41 +1019,45 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     __syncwarp();
 
     unsigned vhist = 0;        // vertical differences, newest in bit 0
-    // residual window (two-vector): win[e] = D(IT+r+1+e, j) while row r is being computed
-    constexpr int NW = Q > 1 ? Q - 1 : 1;
-    int win[NW];
+    // residual window (two-vector), int16 pairs: value e = D(IT+r+1+e, j) while row r is being
+    // computed, in half e&1 of wpk[e/2]
+    using WS = WarpScratch<Q, M>;
+    unsigned wpk[WS::NWP];
 #pragma unroll
-    for (int e = 0; e < NW; ++e) win[e] = 0;
-    win[0] = colT;
+    for (int e = 0; e < WS::NWP; ++e) wpk[e] = 0u;
+    wpk[0] = (unsigned)colT & 0xffffu;
 
     // terms of row rr that do not depend on row rr+1 (computed while row rr+1 closes); branch-free:
     // every candidate is evaluated with in-range indices and the invalid ones are masked
     auto old_terms = [&](int rr) -> int {
         if constexpr (TV) {
-            constexpr int NC = 1 + (Q - 1) + G;
-            int cand[NC];
-            int k = 0;
-            cand[k++] = (int)ws.pm[rr][c];
+            int best = (int)ws.pm[rr][c];
             // residual splits k in [i+2, IT+ce], ce the end of the first group starting after row rr
             // (k = i+1 is the D(i+1,j) term of the row loop); on a group's first row they cover that
             // whole group, so no term of a row waits on the group its previous row completes
-            const int ce = (rr / Q + 1) * Q;
+            unsigned ra = 0u, rb = 0u;
 #pragma unroll
-            for (int e = 0; e < Q - 1; ++e) {
-                const int kk = rr + 2 + e;
-                const int ix = min(kk, T);
-                const int v = (int)dg[rr][ix - 1] + win[e];
-                cand[k++] = (kk <= ce) ? v : kNeg16;
+            for (int k4 = 0; k4 < WS::NWPA / 4; ++k4) {
+                const uint4 a = reinterpret_cast<const uint4 *>(&ws.rpk[rr][0])[k4];
+                if (4 * k4 + 0 < WS::NWP) ra = __viaddmax_s16x2(a.x, wpk[min(4 * k4 + 0, WS::NWP - 1)], ra);
+                if (4 * k4 + 1 < WS::NWP) rb = __viaddmax_s16x2(a.y, wpk[min(4 * k4 + 1, WS::NWP - 1)], rb);
+                if (4 * k4 + 2 < WS::NWP) ra = __viaddmax_s16x2(a.z, wpk[min(4 * k4 + 2, WS::NWP - 1)], ra);
+                if (4 * k4 + 3 < WS::NWP) rb = __viaddmax_s16x2(a.w, wpk[min(4 * k4 + 3, WS::NWP - 1)], rb);
             }
-            // full groups of tile column I after that one (g*q > rr), complete before row rr+1
+            best = max(best, hmax2(__vmaxs2(ra, rb)));
+            // full groups of tile column I after that one (g*q > rr; the others carry A = -32768),
+            // complete before row rr+1
+            int gm = (int)0x80000000u;
 #pragma unroll
-            for (int gl = 0; gl < G; ++gl) {
-                const uint32_t f = drf[rr][gl];
-                const uint32_t cb = ws.cbc[gl][c];
-                const int v = rlookup<Q>(Rs, hrow_offset<Q>((int)(f & C::BMASK)), (int)(cb & C::BMASK));
-                cand[k++] = (gl * Q > rr) ? (int)(f >> 16) + (int)(cb >> 16) + v : kNeg16;
+            for (int g4 = 0; g4 < WS::GA / 4; ++g4) {
+                const uint4 gv = reinterpret_cast<const uint4 *>(&ws.gw[rr][0])[g4];
+                const uint4 cv = reinterpret_cast<const uint4 *>(&ws.cbc[c][0])[g4];
+                if (4 * g4 + 0 < G) gm = max(gm, group_term<Q>(Rs, gv.x, cv.x));
+                if (4 * g4 + 1 < G) gm = max(gm, group_term<Q>(Rs, gv.y, cv.y));
+                if (4 * g4 + 2 < G) gm = max(gm, group_term<Q>(Rs, gv.z, cv.z));
+                if (4 * g4 + 3 < G) gm = max(gm, group_term<Q>(Rs, gv.w, cv.w));
             }
-            return tree_max<NC>(cand);
+            return max(best, gm >> 16);
         } else {
             // every split with D(k,j) in this tile column: rows not yet done hold the sentinel
             unsigned acc2[4] = {0u, 0u, 0u, 0u};
@@ -1008,7 +1075,6 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         }
     };
 
-    uint32_t last_cb = 0;      // feature of the column group completed most recently
     // publishes row r (value d of this lane's column): tile copy, row-major store, vertical and
     // horizontal difference vectors
     auto publish = [&](int r, int d, int below_prev) {
@@ -1020,8 +1086,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             const bool done = r >= 1 && (r - 1) % Q == 0;   // group rows gl*q+1 .. gl*q+q complete
             const int gl = max(r - 1, 0) / Q;
             const uint32_t cb = ((uint32_t)d << 16) | (vhist & C::BMASK);
-            ws.cbc[done ? gl : G][c] = cb;
-            last_cb = done ? cb : last_cb;
+            if (done) ws.cbc[c][gl] = cb;
             if (done && valid) P.cf[sd.cf_off + (size_t)(I * G + gl) * Np + j] = cb;
         } else {
             // row r joins the column pairs used by the rows above
@@ -1122,9 +1187,10 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             publish(r, d, below);
             below = d;
             if constexpr (TV) {
+                // the window moves down one row: value e+1 <- value e, value 0 <- d
 #pragma unroll
-                for (int e = NW - 1; e > 0; --e) win[e] = win[e - 1];
-                win[0] = d;
+                for (int e = WS::NWP - 1; e > 0; --e) wpk[e] = __byte_perm(wpk[e - 1], wpk[e], 0x5432);
+                wpk[0] = __byte_perm((unsigned)d, wpk[0], 0x5410);
             }
         }
     }
@@ -1193,7 +1259,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             if constexpr (TV) {
 #pragma unroll
                 for (int gl = 0; gl < G; ++gl) {
-                    const uint32_t cf = ws.cbc[gl][c];
+                    const uint32_t cf = ws.cbc[c][gl];
                     cs.lB0[gl] = (int)(cf >> 16);
                     cs.lC0[gl] = (int)(cf & C::BMASK);
                 }
