@@ -134,6 +134,14 @@ static __device__ __forceinline__ bool wait_smem_geq(const int *p, int target, i
     return wait_smem_geq_slow(p, target, error, timeout_ns, lane);
 }
 
+// 16-byte global -> shared copies that bypass L1 (both addresses 16-byte aligned)
+static __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+static __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+static __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 static __device__ __forceinline__ int lds16(const int16_t *p) { return (int)*p; }
 static __device__ __forceinline__ int ldcg16(const int16_t *p) { return (int)__ldcg(p); }
 
@@ -164,6 +172,9 @@ struct __align__(16) WarpScratch {
     static constexpr int NWP = (Q > 2 ? Q : 2) / 2;   // two-vector residual window: Q-1 values in pairs
     static constexpr int NWPA = (NWP + 3) / 4 * 4;     // ... padded to 16-byte rows
     static constexpr int GA = (G + 3) / 4 * 4;         // groups padded to 16-byte rows
+    // column mode copies a tile's P slot into shared memory with 16-byte cp.async (T*T a multiple of
+    // four ints; left out where the per-block shared memory would not hold it)
+    static constexpr bool PB = (T * T) % 4 == 0 && !(M == kTwoVector && Q >= 10);
     union {
         struct {                       // chunk tasks
             int2 rf[G][32];            // FAR staging (two-vector): (A, h-row byte offset)
@@ -175,6 +186,7 @@ struct __align__(16) WarpScratch {
             int16_t tile1[T + 1][33];  // second output buffer: tiles alternate between tile and tile1
             uint32_t rfo[2][LF][G];    // row features of the last two tiles (two-vector), read by the
                                        // warp of the next column
+            alignas(16) int pbuf[PB ? T * T : 4];  // the tile's P slot (far partial max), row-major
         };
     };
     alignas(16) int16_t lrow[2][LR][32];  // NEAR late blocks (plain): rows of tiles (I,J-1), (I,I+1)
@@ -205,6 +217,7 @@ struct ScratchChecks {
     static_assert(offsetof(WS, y) % 16 == 0, "y must be 16-byte aligned");
     static_assert(offsetof(WS, rows) % 16 == 0, "rows must be 16-byte aligned");
     static_assert(offsetof(WS, lrow) % 16 == 0, "lrow must be 16-byte aligned");
+    static_assert(offsetof(WS, pbuf) % 16 == 0, "pbuf is written by 16-byte cp.async");
     static_assert(offsetof(WS, lrf) % 16 == 0, "lrf must be 16-byte aligned");
     static_assert(offsetof(WS, cbc) % 16 == 0 && offsetof(WS, gw) % 16 == 0 && offsetof(WS, rpk) % 16 == 0,
                   "cbc, gw and rpk rows are read as uint4");
@@ -697,9 +710,22 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll
         for (int v = 0; v < 16; ++v) lcol[k][v] = 0;
     }
+    // column mode: the tile's P slot goes to shared memory by cp.async, at once when its chunk counter
+    // was already seen complete (the copy then overlaps the wait for the left neighbour)
+    constexpr bool PBC = COL && WarpScratch<Q, M>::PB;
+    auto p_copy = [&]() {
+        if constexpr (PBC) {
+            const int4 *src = reinterpret_cast<const int4 *>(slot);
+            int4 *dst = reinterpret_cast<int4 *>(ws.pbuf);
+#pragma unroll
+            for (int k = lane; k < T * T / 4; k += 32) cp_async16(dst + k, src + k);
+            cp_async_commit();
+        }
+    };
     if constexpr (COL) {
         // the next column's warp must have read the tile two back before its buffer is rewritten
         if (cs.consumer && cs.k >= 2 && !wait_smem_geq(&ws.consumed, cs.k - 1, P.error, P.timeout_ns, lane)) return 0;
+        if (early) p_copy();
         // left neighbour (I, J-1), from the warp of column J-1 in this CTA or else through its flag; it
         // implies every tile of row I to its left, (I,I) and (I,I+1) among them.  The bottom neighbour
         // (I+1, J) is this warp's previous tile.  A complete chunk counter (seen before the last
@@ -811,9 +837,10 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         }
     } else {
         if (t >= 1 && early) {
-            if (prod) {
-                if (!wait_smem_geq(&prod->produced, cs.k, P.error, P.timeout_ns, lane)) return 0;
-            } else if (!warp_wait_geq(flags + I * NT + (J - 1), 1, P, lane)) {
+            const bool ok = prod ? wait_smem_geq(&prod->produced, cs.k, P.error, P.timeout_ns, lane)
+                                 : warp_wait_geq(flags + I * NT + (J - 1), 1, P, lane);
+            if (!ok) {
+                if constexpr (PBC) cp_async_wait_all();   // no copy is left in flight
                 return 0;
             }
         }
@@ -905,8 +932,16 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     // partial max of the FAR chunks (middle blocks I+2 .. J-2)
     if (nfar > 0) {
         if (!early && !warp_wait_geq(P.cnt + sd.cnt_off + I * NT + J, nfar, P, lane)) return 0;
+        if constexpr (PBC) {
+            if (!early) p_copy();
+            cp_async_wait_all();
+            __syncwarp();
 #pragma unroll
-        for (int r = 0; r < T; ++r) acc[r] = valid ? __ldcg(slot + r * T + c) : 0;
+            for (int r = 0; r < T; ++r) acc[r] = valid ? ws.pbuf[r * T + c] : 0;
+        } else {
+#pragma unroll
+            for (int r = 0; r < T; ++r) acc[r] = valid ? __ldcg(slot + r * T + c) : 0;
+        }
         if (P.trace) tdeps[1] = (long long)gtimer();
     } else {
 #pragma unroll
@@ -997,9 +1032,14 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     if (valid) {
 #pragma unroll
         for (int r = 0; r < T; ++r) ws.pm[r][c] = (int16_t)acc[r];
-        if (nfar > 0) {
+    }
+    if (nfar > 0) {   // ring slot reused by tile (I, J+kRing)
+        if constexpr (PBC) {
 #pragma unroll
-            for (int r = 0; r < T; ++r) __stcg(slot + r * T + c, 0);   // ring slot reused by tile (I, J+kRing)
+            for (int k = lane; k < T * T / 4; k += 32) __stcg(reinterpret_cast<int4 *>(slot) + k, make_int4(0, 0, 0, 0));
+        } else if (valid) {
+#pragma unroll
+            for (int r = 0; r < T; ++r) __stcg(slot + r * T + c, 0);
         }
     }
     const long long tfar = P.trace ? (long long)gtimer() : 0;
