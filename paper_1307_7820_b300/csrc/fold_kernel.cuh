@@ -177,7 +177,9 @@ struct __align__(16) WarpScratch {
     static constexpr bool PB = (T * T) % 4 == 0 && !(M == kTwoVector && Q >= 10);
     union {
         struct {                       // chunk tasks
-            int2 rf[G][32];            // FAR staging (two-vector): (A, h-row byte offset)
+            int2 rf[G][32];            // STRIP staging (two-vector): (A in both halves, h-row byte offset)
+            alignas(16) uint32_t rfw[PL ? 1 : 32][PL ? 4 : GA];  // FAR staging (two-vector): per row,
+                                       // (A << 16 | R-row offset) of each group
             uint32_t scv[PL ? 1 : G][PL ? 1 : SS + SS / 2][32];  // STRIP staging (two-vector): per group,
                                        // the lane's column bits for SS columns and SS/2 packed base pairs
             alignas(16) int16_t rows[LR][32];  // FAR staging (plain): row strips (uint4 access)
@@ -216,6 +218,8 @@ struct ScratchChecks {
     using WS = WarpScratch<Q, M>;
     static_assert(offsetof(WS, y) % 16 == 0, "y must be 16-byte aligned");
     static_assert(offsetof(WS, rows) % 16 == 0, "rows must be 16-byte aligned");
+    static_assert(offsetof(WS, rfw) % 16 == 0, "rfw rows are read as uint4");
+    static_assert(offsetof(WS, rf) % 16 == 0, "rf row pairs are read as uint4");
     static_assert(offsetof(WS, lrow) % 16 == 0, "lrow must be 16-byte aligned");
     static_assert(offsetof(WS, pbuf) % 16 == 0, "pbuf is written by 16-byte cp.async");
     static_assert(offsetof(WS, lrf) % 16 == 0, "lrf must be 16-byte aligned");
@@ -268,47 +272,27 @@ __device__ __forceinline__ int group_term(const uint8_t *Rs, uint32_t w, uint32_
     }
 }
 
-// ---------------------------------------------------------------- far blocks
-// Two-vector: for the groups of middle tile column K, m[r] (lane = column c)
-// = max(m[r], A(i,g) + B(g,j) + R[h(i,g)][c(g,j)]), Eq. 3.
+// A row feature (A << 16 | h) as the word group_term takes: h replaced by its R-row offset
+// (kept as h for nibble tables, whose offsets need more than 16 bits).
 template <int Q>
-__device__ __forceinline__ void far_block_tv(const FoldParams &P, const SeqDesc &sd, int I, int J, int K, int *m,
-                                             WarpScratch<Q, kTwoVector> &ws, const uint8_t *Rs, int lane) {
-    using C = Cfg<Q, kTwoVector>;
-    constexpr int T = C::T, G = C::G;
-    const int Np = sd.Np, NG = Np / Q;
-    const uint32_t *RF = P.rf + sd.rf_off;
-    const uint32_t *CF = P.cf + sd.cf_off;
-    const bool valid = lane < T;
-    int B[G], Cv[G];
-#pragma unroll
-    for (int gl = 0; gl < G; ++gl) {
-        int g = K * G + gl;
-        uint32_t cf = valid ? __ldcg(CF + (size_t)g * Np + J * T + lane) : 0u;
-        uint32_t rf = valid ? __ldcg(RF + (size_t)(I * T + lane) * NG + g) : 0u;
-        B[gl] = (int)(cf >> 16);
-        Cv[gl] = (int)(cf & C::BMASK);
-        ws.rf[gl][lane] = make_int2((int)(rf >> 16), hrow_offset<Q>((int)(rf & C::BMASK)));
-    }
-    __syncwarp();
-#pragma unroll
-    for (int gl = 0; gl < G; ++gl) {
-#pragma unroll
-        for (int r = 0; r < T; ++r) {
-            int2 f = ws.rf[gl][r];
-            int v = rlookup<Q>(Rs, f.y, Cv[gl]);
-            m[r] = max(m[r], f.x + B[gl] + v);
-        }
-    }
-    __syncwarp();
+__device__ __forceinline__ uint32_t group_word(uint32_t f) {
+    constexpr unsigned BM = (1u << (Q - 1)) - 1;
+    if constexpr (Q >= 10) return f;
+    else return (f & 0xffff0000u) | (uint32_t)hrow_offset<Q>((int)(f & BM));
 }
 
-// A chunk of middle blocks [Ka, Kb]: the features of block K+1 are loaded while
-// block K is evaluated, so each block's L2 latency overlaps the previous block.
+// ---------------------------------------------------------------- far blocks
+// Two-vector, a chunk of middle blocks [Ka, Kb] of tile (I,J): for each group g of the blocks,
+// m[r] (lane = column c) = max(m[r], A(i,g) + B(g,j) + R[h(i,g)][c(g,j)]), Eq. 3.  The rows'
+// features go to shared memory as words (A << 16 | R-row offset), four groups per 16-byte
+// broadcast load; the lane's column feature (B << 16 | c) is used as loaded.  The features of
+// block K+1 are loaded while block K is evaluated, so each block's L2 latency overlaps the
+// previous block.  m[] is kept scaled by 2^16 inside (see group_term).
 template <int Q>
 __device__ __forceinline__ void far_chunk_tv(const FoldParams &P, const SeqDesc &sd, int I, int J, int Ka, int Kb,
                                              int *m, WarpScratch<Q, kTwoVector> &ws, const uint8_t *Rs, int lane) {
     using C = Cfg<Q, kTwoVector>;
+    using WS = WarpScratch<Q, kTwoVector>;
     constexpr int T = C::T, G = C::G;
     const int Np = sd.Np, NG = Np / Q;
     const uint32_t *RF = P.rf + sd.rf_off;
@@ -321,14 +305,21 @@ __device__ __forceinline__ void far_chunk_tv(const FoldParams &P, const SeqDesc 
         cfn[gl] = valid ? __ldcg(CF + (size_t)g * Np + J * T + lane) : 0u;
         rfn[gl] = valid ? __ldcg(RF + (size_t)(I * T + lane) * NG + g) : 0u;
     }
-    for (int K = Ka; K <= Kb; ++K) {
-        int B[G], Cv[G];
 #pragma unroll
-        for (int gl = 0; gl < G; ++gl) {
-            B[gl] = (int)(cfn[gl] >> 16);
-            Cv[gl] = (int)(cfn[gl] & C::BMASK);
-            ws.rf[gl][lane] = make_int2((int)(rfn[gl] >> 16), hrow_offset<Q>((int)(rfn[gl] & C::BMASK)));
+    for (int r = 0; r < T; ++r) m[r] = (int)((unsigned)m[r] << 16);
+    for (int K = Ka; K <= Kb; ++K) {
+        uint32_t cb[G];
+        uint32_t w[WS::GA];
+#pragma unroll
+        for (int gl = 0; gl < WS::GA; ++gl) {
+            const uint32_t f = gl < G ? rfn[min(gl, G - 1)] : 0u;
+            w[gl] = (f & 0xffff0000u) | (C::NIB ? (f & C::BMASK) : (uint32_t)hrow_offset<Q>((int)(f & C::BMASK)));
         }
+#pragma unroll
+        for (int gl = 0; gl < G; ++gl) cb[gl] = cfn[gl];
+#pragma unroll
+        for (int g4 = 0; g4 < WS::GA / 4; ++g4)
+            reinterpret_cast<uint4 *>(&ws.rfw[lane][0])[g4] = make_uint4(w[4 * g4], w[4 * g4 + 1], w[4 * g4 + 2], w[4 * g4 + 3]);
         if (K < Kb) {   // prefetch the next block
 #pragma unroll
             for (int gl = 0; gl < G; ++gl) {
@@ -339,16 +330,20 @@ __device__ __forceinline__ void far_chunk_tv(const FoldParams &P, const SeqDesc 
         }
         __syncwarp();
 #pragma unroll
-        for (int gl = 0; gl < G; ++gl) {
+        for (int r = 0; r < T; ++r) {
 #pragma unroll
-            for (int r = 0; r < T; ++r) {
-                const int2 f = ws.rf[gl][r];
-                const int v = rlookup<Q>(Rs, f.y, Cv[gl]);
-                m[r] = max(m[r], f.x + B[gl] + v);
+            for (int g4 = 0; g4 < WS::GA / 4; ++g4) {
+                const uint4 w4 = reinterpret_cast<const uint4 *>(&ws.rfw[r][0])[g4];
+                if (4 * g4 + 0 < G) m[r] = max(m[r], group_term<Q>(Rs, w4.x, cb[min(4 * g4 + 0, G - 1)]));
+                if (4 * g4 + 1 < G) m[r] = max(m[r], group_term<Q>(Rs, w4.y, cb[min(4 * g4 + 1, G - 1)]));
+                if (4 * g4 + 2 < G) m[r] = max(m[r], group_term<Q>(Rs, w4.z, cb[min(4 * g4 + 2, G - 1)]));
+                if (4 * g4 + 3 < G) m[r] = max(m[r], group_term<Q>(Rs, w4.w, cb[min(4 * g4 + 3, G - 1)]));
             }
         }
         __syncwarp();
     }
+#pragma unroll
+    for (int r = 0; r < T; ++r) m[r] >>= 16;
 }
 
 // Plain: m[r] holds two packed int16 partial maxima; splits k in [KT+1, KT+T].
@@ -502,15 +497,23 @@ __device__ __forceinline__ void far_strip_tv(const FoldParams &P, const SeqDesc 
             for (int s2 = 0; s2 < S; ++s2) cv[s2] = (int)ws.scv[gl][s2][lane];
 #pragma unroll
             for (int p2 = 0; p2 < S / 2; ++p2) b2[p2] = ws.scv[gl][S + p2][lane];
+            // two rows' features per 16-byte broadcast load
 #pragma unroll
-            for (int r = 0; r < T; ++r) {
-                const int2 f = ws.rf[gl][r];
+            for (int r2 = 0; r2 < (T + 1) / 2; ++r2) {
+                const uint4 f2 = reinterpret_cast<const uint4 *>(&ws.rf[gl][0])[r2];
 #pragma unroll
-                for (int p2 = 0; p2 < S / 2; ++p2) {
-                    const unsigned v0 = (unsigned)rlookup<Q>(Rs, f.y, cv[2 * p2]);
-                    const unsigned v1 = (unsigned)rlookup<Q>(Rs, f.y, cv[2 * p2 + 1]);
-                    const unsigned t = (unsigned)f.x + b2[p2] + (v1 * 65536u + v0);
-                    m2[p2][r] = __vmaxs2(m2[p2][r], t);
+                for (int u = 0; u < 2; ++u) {
+                    const int r = 2 * r2 + u;
+                    if (r >= T) break;
+                    const unsigned fx = u ? f2.z : f2.x;
+                    const int fy = (int)(u ? f2.w : f2.y);
+#pragma unroll
+                    for (int p2 = 0; p2 < S / 2; ++p2) {
+                        const unsigned v0 = (unsigned)rlookup<Q>(Rs, fy, cv[2 * p2]);
+                        const unsigned v1 = (unsigned)rlookup<Q>(Rs, fy, cv[2 * p2 + 1]);
+                        const unsigned t = fx + b2[p2] + (v1 * 65536u + v0);
+                        m2[p2][r] = __vmaxs2(m2[p2][r], t);
+                    }
                 }
             }
         }
@@ -647,7 +650,7 @@ struct NearCol {
     WarpScratch<Q, M> *prod;      // scratch of the warp of column J-1 in this CTA, or null
     bool consumer;                // the warp of column J+1 runs in this CTA and reads this warp's tiles
     unsigned Wp[16];              // W[c'][c] of tile (J,J), packed pairs (set by tile 0)
-    int lB0[G], lC0[G];           // two-vector: features of middle block J-1 in column j (set by tile 1)
+    uint32_t lcb0[G];             // two-vector: features (B << 16 | c) of middle block J-1 in column j (set by tile 1)
     unsigned lcol0[16];           // plain: column j of tile (J-1,J), packed pairs (set by tile 1)
     int colT;                     // D(IT, j) of the tile just finished: row 0 of the next tile's bottom neighbour
     bool cnt_ok;                  // the next tile's chunk counter was complete when the last tile released
@@ -701,12 +704,12 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 
     // ---- inputs from tiles finished long before the neighbours, all loads in flight at once
     unsigned Wp[16];           // packed W[c'][c] = D(JT+c'+1, j) for c' < c, sentinel otherwise
-    int lB[2][G], lC[2][G];    // late-block column features (two-vector)
+    uint32_t lcb[2][G];        // late-block column features (B << 16 | c) (two-vector)
     unsigned lcol[2][16];      // late-block columns as packed pairs (plain)
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
 #pragma unroll
-        for (int gl = 0; gl < G; ++gl) { lB[k][gl] = 0; lC[k][gl] = 0; }
+        for (int gl = 0; gl < G; ++gl) lcb[k][gl] = 0u;
 #pragma unroll
         for (int v = 0; v < 16; ++v) lcol[k][v] = 0;
     }
@@ -778,12 +781,10 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll
                 for (int gl = 0; gl < G; ++gl) {
                     if constexpr (COL) {
-                        lB[0][gl] = cs.lB0[gl];
-                        lC[0][gl] = cs.lC0[gl];
+                        lcb[0][gl] = cs.lcb0[gl];
                     } else {
                         const uint32_t cf = __ldcg(CF + (size_t)((J - 1) * G + gl) * Np + j);
-                        lB[0][gl] = (int)(cf >> 16);
-                        lC[0][gl] = (int)(cf & C::BMASK);
+                        lcb[0][gl] = cf;
                     }
                 }
             }
@@ -797,7 +798,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
                     const uint32_t hw = C::NIB ? (fv[e] & C::BMASK) : (uint32_t)hrow_offset<Q>((int)(fv[e] & C::BMASK));
                     const uint32_t aw = (gl * Q > rw) ? (fv[e] & 0xffff0000u) : 0x80000000u;
                     ws.gw[rw][gl] = aw | hw;
-                    lrf1[rw][gl] = fb[e];
+                    lrf1[rw][gl] = group_word<Q>(fb[e]);
                 }
             }
         } else {
@@ -882,8 +883,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             for (int gl = 0; gl < G; ++gl) {
                 // column mode: the features of block I+1 are this warp's previous tile's
                 const uint32_t cf = COL ? ws.cbc[c][gl] : __ldcg(CF + (size_t)((I + 1) * G + gl) * Np + j);
-                lB[1][gl] = (int)(cf >> 16);
-                lC[1][gl] = (int)(cf & C::BMASK);
+                lcb[1][gl] = cf;
             }
         }
         // this tile's column groups start as (B, c) = (0, 0): a group that is not complete below a
@@ -951,7 +951,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int idx = e * 32 + lane;
-            if (idx < T * G) ws.lrf[0][idx / G][idx % G] = fa[e];
+            if (idx < T * G) ws.lrf[0][idx / G][idx % G] = group_word<Q>(fa[e]);
         }
     } else {
         uint4 *dst = reinterpret_cast<uint4 *>(&ws.lrow[0][lane][0]);
@@ -983,6 +983,9 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     }
     // the two late middle blocks for every row at once (independent lookups, high ILP)
     if constexpr (TV) {
+        // acc is scaled by 2^16 while the group terms are merged (see group_term)
+#pragma unroll
+        for (int r = 0; r < T; ++r) acc[r] = (int)((unsigned)acc[r] << 16);
 #pragma unroll
         for (int kb = 0; kb < 2; ++kb) {
             if (kb == 0 ? lateA : lateB) {
@@ -1001,13 +1004,12 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
                         for (int gl = 0; gl < G; ++gl) fr[gl] = kb == 0 ? ws.lrf[0][r][gl] : lrf1[r][gl];
                     }
 #pragma unroll
-                    for (int gl = 0; gl < G; ++gl) {
-                        const int v = rlookup<Q>(Rs, hrow_offset<Q>((int)(fr[gl] & C::BMASK)), lC[kb][gl]);
-                        acc[r] = max(acc[r], (int)(fr[gl] >> 16) + lB[kb][gl] + v);
-                    }
+                    for (int gl = 0; gl < G; ++gl) acc[r] = max(acc[r], group_term<Q>(Rs, fr[gl], lcb[kb][gl]));
                 }
             }
         }
+#pragma unroll
+        for (int r = 0; r < T; ++r) acc[r] >>= 16;
     } else {
 #pragma unroll
         for (int kb = 0; kb < 2; ++kb) {
@@ -1300,8 +1302,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll
                 for (int gl = 0; gl < G; ++gl) {
                     const uint32_t cf = ws.cbc[c][gl];
-                    cs.lB0[gl] = (int)(cf >> 16);
-                    cs.lC0[gl] = (int)(cf & C::BMASK);
+                    cs.lcb0[gl] = cf;
                 }
             } else {
 #pragma unroll
