@@ -402,10 +402,31 @@ static __device__ __forceinline__ int hmax2(unsigned a) {
     return max((int)(short)(a & 0xffffu), (int)(short)(a >> 16));
 }
 
+// The queue's next task for a worker: claimed while the worker finishes its current chunk, right
+// after the chunk's merges are issued, so that the claim's round trips (queue atomic, task load)
+// overlap the merges' completion.  The claim comes only the merge's duration early, so tasks still
+// start in about list order.
+struct NextTask {
+    int *qhead;
+    int qbase, qlimit;
+    const int4 *tasks;
+    int idx;
+    int4 tk;
+    bool have;
+    __device__ __forceinline__ void claim(int lane) {
+        int i = 0;
+        if (lane == 0) i = qbase + atomicAdd(qhead, 1);
+        i = __shfl_sync(FULL, i, 0);
+        idx = i;
+        tk = i < qlimit ? tasks[i] : make_int4(0, 0, 0, 0);
+        have = true;
+    }
+};
+
 // ---------------------------------------------------------------- FAR task
 template <int Q, int M>
 __device__ __forceinline__ long long run_far(const FoldParams &P, const SeqDesc &sd, int I, int J, int Ka, int Kb,
-                        WarpScratch<Q, M> &ws, const uint8_t *Rs, int lane, long long *tdeps) {
+                        WarpScratch<Q, M> &ws, const uint8_t *Rs, int lane, long long *tdeps, NextTask &nt) {
     constexpr int T = Cfg<Q, M>::T;
     const int NT = sd.NT;
     int *flags = P.flags + sd.flag_off;
@@ -437,6 +458,7 @@ __device__ __forceinline__ long long run_far(const FoldParams &P, const SeqDesc 
         for (int r = 0; r < T; ++r)
             if (m[r] > 0) atomicMax(slot + r * T + lane, m[r]);
     }
+    nt.claim(lane);
     __threadfence();
     __syncwarp();
     if (lane == 0) atomicAdd(P.cnt + sd.cnt_off + I * NT + J, 1);
@@ -579,7 +601,7 @@ __device__ __forceinline__ void far_strip_plain(const FoldParams &P, const SeqDe
 template <int Q, int M>
 __device__ __forceinline__ long long run_far_strip(const FoldParams &P, const SeqDesc &sd, int I, int J0, int Ka,
                                                    int Kb, WarpScratch<Q, M> &ws, const uint8_t *Rs, int lane,
-                                                   long long *tdeps) {
+                                                   long long *tdeps, NextTask &nt) {
     constexpr int T = Cfg<Q, M>::T;
     constexpr int S = strip_of(Q, M);
     const int NT = sd.NT;
@@ -634,6 +656,7 @@ __device__ __forceinline__ long long run_far_strip(const FoldParams &P, const Se
             }
         }
     }
+    nt.claim(lane);
     __threadfence();
     __syncwarp();
     if (lane < Seff) atomicAdd(P.cnt + sd.cnt_off + I * NT + J0 + lane, 1);
@@ -1393,16 +1416,20 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
         }
         return;
     }
-    int *qhead = far_role ? P.queue_head_far : P.queue_head;
-    const int qbase = far_role ? P.nnear : 0;
-    const int qlimit = (split && !far_role) ? P.nnear : P.ntasks;
+    NextTask nt;
+    nt.qhead = far_role ? P.queue_head_far : P.queue_head;
+    nt.qbase = far_role ? P.nnear : 0;
+    nt.qlimit = (split && !far_role) ? P.nnear : P.ntasks;
+    nt.tasks = P.tasks;
+    nt.have = false;
+    int err = 0;   // the error word as read when the previous task started
     for (;;) {
-        int idx = 0;
-        if (lane == 0) idx = qbase + atomicAdd(qhead, 1);
-        idx = __shfl_sync(FULL, idx, 0);
-        if (idx >= qlimit) break;
-        if (*(volatile int *)P.error != 0) break;
-        const int4 tk = P.tasks[idx];
+        if (!nt.have) nt.claim(lane);
+        nt.have = false;
+        const int idx = nt.idx;
+        const int4 tk = nt.tk;
+        if (idx >= nt.qlimit || err != 0) break;
+        err = ld_relaxed(P.error);   // checked before the next task
         const SeqDesc sd = P.seqs[tk.x];
         const int I = task_I(tk.y), J = task_J(tk.y);
         long long t0 = 0, tdeps[4] = {0, 0, 0, 0};
@@ -1417,8 +1444,8 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
             none.cnt_ok = false;
             tmid = run_near<Q, M, false>(P, sd, I, J, tk.z, ws, Rs, lane, tdeps, none);
         }
-        else if (ty == kTaskFar) tmid = run_far<Q, M>(P, sd, I, J, tk.z, tk.w, ws, Rs, lane, tdeps);
-        else tmid = run_far_strip<Q, M>(P, sd, I, J, tk.z, tk.w, ws, Rs, lane, tdeps);
+        else if (ty == kTaskFar) tmid = run_far<Q, M>(P, sd, I, J, tk.z, tk.w, ws, Rs, lane, tdeps, nt);
+        else tmid = run_far_strip<Q, M>(P, sd, I, J, tk.z, tk.w, ws, Rs, lane, tdeps, nt);
         if (P.trace && lane == 0) {
             long long *rec = P.trace + (size_t)idx * kTraceWords;
             rec[0] = ((long long)(blockIdx.x * kWarpsPerCta + warp) << 32) | (unsigned)idx;
