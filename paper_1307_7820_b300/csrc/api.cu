@@ -23,7 +23,7 @@ namespace fold {
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-int kc_auto(int NT) { return std::min(64, std::max(4, NT / 24)); }
+int kc_auto(int NT) { return std::min(64, std::max(4, NT / 18)); }
 
 // Layout of `count` sequences inside one workspace.  Sections (256-byte
 // aligned): control | results | flags | counters | P ring | codes | Drow |

@@ -413,13 +413,20 @@ struct NextTask {
     int idx;
     int4 tk;
     bool have;
-    __device__ __forceinline__ void claim(int lane) {
-        int i = 0;
-        if (lane == 0) i = qbase + atomicAdd(qhead, 1);
-        i = __shfl_sync(FULL, i, 0);
+    int pending;   // lane 0: the queue atomic's result, read by finish()
+    // the queue atomic goes out here; its result is read by finish()
+    __device__ __forceinline__ void start(int lane) {
+        if (lane == 0) pending = atomicAdd(qhead, 1);
+    }
+    __device__ __forceinline__ void finish(int lane) {
+        const int i = qbase + __shfl_sync(FULL, lane == 0 ? pending : 0, 0);
         idx = i;
         tk = i < qlimit ? tasks[i] : make_int4(0, 0, 0, 0);
         have = true;
+    }
+    __device__ __forceinline__ void claim(int lane) {
+        start(lane);
+        finish(lane);
     }
 };
 
@@ -452,13 +459,14 @@ __device__ __forceinline__ long long run_far(const FoldParams &P, const SeqDesc 
         for (int r = 0; r < T; ++r) m[r] = hmax2(mp[r]);
     }
     const long long tdone = P.trace ? (long long)gtimer() : 0;
+    nt.start(lane);
     int *slot = P.pring + sd.p_off + ((size_t)((J - I) % kRing) * NT + I) * (T * T);
     if (lane < T) {
 #pragma unroll
         for (int r = 0; r < T; ++r)
             if (m[r] > 0) atomicMax(slot + r * T + lane, m[r]);
     }
-    nt.claim(lane);
+    nt.finish(lane);
     __threadfence();
     __syncwarp();
     if (lane == 0) atomicAdd(P.cnt + sd.cnt_off + I * NT + J, 1);
@@ -625,6 +633,7 @@ __device__ __forceinline__ long long run_far_strip(const FoldParams &P, const Se
             for (int r = 0; r < T; ++r) m2[p2][r] = 0u;
         far_strip_tv<Q, S>(P, sd, I, J0, Seff, Ka, Kb, m2, ws, Rs, lane);
         if (P.trace) tdone = (long long)gtimer();
+        nt.start(lane);
         if (lane < T) {
 #pragma unroll
             for (int s2 = 0; s2 < S; ++s2) {
@@ -645,6 +654,7 @@ __device__ __forceinline__ long long run_far_strip(const FoldParams &P, const Se
             for (int r = 0; r < 32; ++r) acc[s2][r] = 0u;
         far_strip_plain<S>(P, sd, I, J0, Seff, Ka, Kb, acc, ws, lane);
         if (P.trace) tdone = (long long)gtimer();
+        nt.start(lane);
 #pragma unroll
         for (int s2 = 0; s2 < S; ++s2) {
             if (s2 >= Seff) continue;
@@ -656,7 +666,7 @@ __device__ __forceinline__ long long run_far_strip(const FoldParams &P, const Se
             }
         }
     }
-    nt.claim(lane);
+    nt.finish(lane);
     __threadfence();
     __syncwarp();
     if (lane < Seff) atomicAdd(P.cnt + sd.cnt_off + I * NT + J0 + lane, 1);
