@@ -134,6 +134,12 @@ static __device__ __forceinline__ bool wait_smem_geq(const int *p, int target, i
     return wait_smem_geq_slow(p, target, error, timeout_ns, lane);
 }
 
+// max into global memory without returning the old value (a reduction, not an atomic: nothing
+// comes back to the SM; the fence that follows the merges orders them before the chunk count)
+static __device__ __forceinline__ void red_max(int *p, int v) {
+    asm volatile("red.relaxed.gpu.global.max.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // 16-byte global -> shared copies that bypass L1 (both addresses 16-byte aligned)
 static __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -464,7 +470,7 @@ __device__ __forceinline__ long long run_far(const FoldParams &P, const SeqDesc 
     if (lane < T) {
 #pragma unroll
         for (int r = 0; r < T; ++r)
-            if (m[r] > 0) atomicMax(slot + r * T + lane, m[r]);
+            if (m[r] > 0) red_max(slot + r * T + lane, m[r]);
     }
     nt.finish(lane);
     __threadfence();
@@ -642,7 +648,7 @@ __device__ __forceinline__ long long run_far_strip(const FoldParams &P, const Se
 #pragma unroll
                 for (int r = 0; r < T; ++r) {
                     const int v = (s2 & 1) ? (int)(m2[s2 / 2][r] >> 16) : (int)(m2[s2 / 2][r] & 0xffffu);
-                    if (v > 0) atomicMax(slot + r * T + lane, v);
+                    if (v > 0) red_max(slot + r * T + lane, v);
                 }
             }
         }
@@ -662,7 +668,7 @@ __device__ __forceinline__ long long run_far_strip(const FoldParams &P, const Se
 #pragma unroll
             for (int r = 0; r < T; ++r) {
                 const int v = hmax2(acc[s2][r]);
-                if (v > 0) atomicMax(slot + r * T + lane, v);
+                if (v > 0) red_max(slot + r * T + lane, v);
             }
         }
     }
