@@ -12,6 +12,8 @@ Functions (each cites the passage of the paper it follows; see ``oracle.c``):
 * :func:`brute`         -- Section 2 problem statement, exhaustive matchings.
 * :func:`rtable`        -- Section 3.1 preprocessing routine over all vector pairs.
 * :func:`two_vector`    -- Section 3.1, Algorithm 1 (serial two-vector).
+* :func:`two_vector_sliding` -- Section 4, the parallel two-vector algorithm with
+  difference vectors at every cell and groups relative to i.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against brute force, hand-worked fixtures in ``tests/golden/``, closed forms
@@ -75,6 +77,8 @@ def _load():
         lib.oracle_rtable.restype = ctypes.c_long
         lib.oracle_two_vector.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_uint16, i32p, i64p]
         lib.oracle_two_vector.restype = ctypes.c_int
+        lib.oracle_two_vector_sliding.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_uint16, i32p, i64p]
+        lib.oracle_two_vector_sliding.restype = ctypes.c_int
         lib.oracle_traceback.argtypes = [u8p, ctypes.c_int, ctypes.c_uint16, i32p, i32p]
         lib.oracle_traceback.restype = ctypes.c_int
         _lib = lib
@@ -170,4 +174,20 @@ def two_vector(seq: str, q: int, mask: int = MASK6, return_lookups: bool = False
                                    ctypes.byref(nl))
         if rc != 0:
             raise MemoryError("oracle_two_vector failed")
+    return (D, int(nl.value)) if return_lookups else D
+
+
+def two_vector_sliding(seq: str, q: int, mask: int = MASK6, return_lookups: bool = False):
+    """Full table by Section 4's two-vector algorithm with per-cell difference vectors (int32);
+    optionally the number of R lookups made."""
+    lib = _load()
+    c = encode(seq)
+    n = len(c)
+    D = np.zeros((n, n), dtype=np.int32)
+    nl = ctypes.c_int64(0)
+    if n:
+        rc = lib.oracle_two_vector_sliding(_u8(c), n, q, mask, D.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                           ctypes.byref(nl))
+        if rc != 0:
+            raise MemoryError("oracle_two_vector_sliding failed")
     return (D, int(nl.value)) if return_lookups else D

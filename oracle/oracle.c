@@ -21,6 +21,11 @@
  *   oracle_two_vector   Section 3.1, Algorithm 1: column-wise fill with the
  *                       pair term, the two residual loops, the Four-Russians
  *                       loop of table lookups (Eq. 3), and the vector stores.
+ *   oracle_two_vector_sliding
+ *                       Section 4: the parallel two-vector algorithm with
+ *                       difference vectors at every cell and groups relative
+ *                       to i, filled diagonal by diagonal, one column per
+ *                       process.
  *   oracle_traceback    Section 2, the traceback: the argmax of Eq. 1 (D*)
  *                       re-evaluated at each visited cell of a finished table,
  *                       giving one optimal set of pairs.
@@ -260,6 +265,82 @@ int oracle_two_vector(const uint8_t *codes, int n, int q, uint16_t mask, int32_t
     free(R);
     free(hv);
     free(cv);
+    return 0;
+}
+
+/* Section 4, the parallel two-vector algorithm with difference vectors at
+ * every cell (the sliding-window variant).  The fill goes diagonal by diagonal
+ * (iteration d = j - i); within an iteration every column j ("process j") fills
+ * cell (i, j) = (j - d, j):
+ *   1. D(i,j) = D(i+1,j-1) + b(S_i,S_j);
+ *   2. groups relative to i: for k' = 0 .. floor((j-i)/q) - 1, k = i + k'q,
+ *      D(i,j) = max(D(i,j), D(i,k) + D(k+1,j) + R[dH(i,k)][dV(k+1,j)]);
+ *   3. residual splits k = i + floor((j-i)/q)*q .. j-1:
+ *      D(i,j) = max(D(i,j), D(i,k) + D(k+1,j));
+ *   4. the vectors that cell (i,j) completes are stored: dV(i,j), the vertical
+ *      vector of cells D(i..i+q-1, j), and dH(i, j-q+1), the horizontal vector
+ *      of cells D(i, j-q+1..j).
+ * Vectors (the readings used throughout): dH(i,k) has bit p-1 =
+ * D(i,k+p) - D(i,k+p-1) and dV(r,j) has bit p-1 = D(r+p-1,j) - D(r+p,j), for
+ * p = 1..q-1, so that D(i,k) + D(k+1,j) + R[dH(i,k)][dV(k+1,j)] is the best of
+ * the splits D(i,k+p) + D(k+p+1,j), p = 0..q-1.  The section's loop bounds are
+ * garbled in the text; this is the reading in which the groups and the
+ * residual together cover every split k in [i, j-1] (in the D(i,k) + D(k+1,j)
+ * form) exactly once.  D as in oracle_nussinov; lookups (if not NULL) receives
+ * the number of table lookups, sum over cells of floor((j-i)/q). */
+int oracle_two_vector_sliding(const uint8_t *codes, int n, int q, uint16_t mask, int32_t *D, int64_t *lookups) {
+    if (n < 0 || q < 1 || q > 12) return -1;
+    if (lookups) *lookups = 0;
+    if (n == 0) return 0;
+    long nent = 1L << (2 * (q - 1));
+    uint8_t *R = (uint8_t *)malloc((size_t)nent);
+    /* dh[i*n+k] = dH(i,k); dv[r*n+j] = dV(r,j) */
+    uint32_t *dh = (uint32_t *)calloc((size_t)n * n, sizeof(uint32_t));
+    uint32_t *dv = (uint32_t *)calloc((size_t)n * n, sizeof(uint32_t));
+    if (!R || !dh || !dv) { free(R); free(dh); free(dv); return -2; }
+    oracle_rtable(q, R, NULL);
+    memset(D, 0, sizeof(int32_t) * (size_t)n * (size_t)n);
+#define DD(a, b) (((a) < n && (b) >= 0 && (a) <= (b)) ? D[(size_t)(a) * n + (b)] : 0)
+    int64_t nl = 0;
+    for (int d = 1; d < n; ++d) {
+        for (int j = d; j < n; ++j) {
+            const int i = j - d;
+            /* 1. pair term */
+            int best = DD(i + 1, j - 1) + pair_b(mask, codes[i], codes[j]);
+            /* 2. groups relative to i, one lookup each */
+            const int ng = (j - i) / q;
+            for (int kp = 0; kp < ng; ++kp) {
+                const int k = i + kp * q;
+                const unsigned h = dh[(size_t)i * n + k], c = dv[(size_t)(k + 1) * n + j];
+                int v = DD(i, k) + DD(k + 1, j) + R[((long)h << (q - 1)) | c];
+                ++nl;
+                if (v > best) best = v;
+            }
+            /* 3. residual splits */
+            for (int k = i + ng * q; k <= j - 1; ++k) {
+                int v = DD(i, k) + DD(k + 1, j);
+                if (v > best) best = v;
+            }
+            D[(size_t)i * n + j] = best;
+            /* 4. the vectors this cell completes */
+            {
+                uint32_t c = 0;
+                for (int p = 1; p <= q - 1; ++p) c |= (uint32_t)(DD(i + p - 1, j) - DD(i + p, j)) << (p - 1);
+                dv[(size_t)i * n + j] = c;
+            }
+            if (j - q + 1 >= i) {
+                const int k = j - q + 1;
+                uint32_t h = 0;
+                for (int p = 1; p <= q - 1; ++p) h |= (uint32_t)(DD(i, k + p) - DD(i, k + p - 1)) << (p - 1);
+                dh[(size_t)i * n + k] = h;
+            }
+        }
+    }
+#undef DD
+    if (lookups) *lookups = nl;
+    free(R);
+    free(dh);
+    free(dv);
     return 0;
 }
 
