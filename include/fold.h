@@ -61,7 +61,13 @@ enum fold_status {
 
 enum fold_method {
     FOLD_METHOD_TWO_VECTOR = 0, /* Section 3.1 / Section 4: R-table lookups per group of q splits */
-    FOLD_METHOD_PLAIN = 1       /* Section 2 / Section 4: every split evaluated (comparison kernel) */
+    FOLD_METHOD_PLAIN = 1,      /* Section 2 / Section 4: every split evaluated (comparison kernel) */
+    FOLD_METHOD_SLIDING = 2     /* Section 4 as printed: one warp per column filling it bottom to top,
+                                   groups of q splits relative to i and difference vectors stored at
+                                   every cell (a second kernel organisation, kept for comparison).
+                                   Single folds only (fold_score, fold_score_dev, fold_structure*);
+                                   fold_batch, serving and the autotuner return FOLD_EINVAL.  Its
+                                   workspace holds D plus two n*n uint32 vector tables (10*n^2 bytes). */
 };
 
 enum fold_option {

@@ -16,6 +16,7 @@
 #include "fold_common.h"
 #include "kernels.h"
 #include "schedule.h"
+#include "sliding.h"
 
 using namespace fold;
 
@@ -336,8 +337,79 @@ int single_schedule(fold_ctx *ctx, int n, const Plan &pl, const int4 **tasks, in
 }
 
 // Enqueues the fold of one sequence whose codes are in device memory.
+// Section 4's organisation (FOLD_METHOD_SLIDING): its own workspace layout and kernel.
+static int enqueue_sliding(fold_ctx *ctx, const uint8_t *d_codes, int n, uint8_t *ws, size_t ws_bytes, int32_t *d_out,
+                           int16_t *d_D, cudaStream_t st) {
+    const SlidingLayout L = sliding_layout(n);
+    if (ws_bytes < L.bytes) return FOLD_ENOMEM;
+    cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_bytes, st);
+    if (e == cudaSuccess && n > 0) e = cudaMemsetAsync(ws + L.off_drow, 0, (size_t)n * n * 2, st);
+    if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(ws + L.off_codes, d_codes, (size_t)n, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    int *control = reinterpret_cast<int *>(ws + L.off_control);
+    int *results = reinterpret_cast<int *>(ws + L.off_results);
+    if (n >= 2) {
+        SlidingParams p;
+        p.codes = ws + L.off_codes;
+        p.n = n;
+        p.drow = reinterpret_cast<int16_t *>(ws + L.off_drow);
+        p.H = reinterpret_cast<uint32_t *>(ws + L.off_H);
+        p.V = reinterpret_cast<uint32_t *>(ws + L.off_V);
+        p.progress = reinterpret_cast<int *>(ws + L.off_progress);
+        p.next_col = control;
+        p.error = control + 1;
+        p.result = results;
+        p.rtab = ctx->d_rpacked;
+        p.pair64 = ctx->pair64;
+        p.timeout_ns = ctx->timeout_ms * 1000000LL;
+        if (ctx->timing) {
+            if (!ctx->ev0) {
+                if ((e = cudaEventCreate(&ctx->ev0)) != cudaSuccess) return status_from_cuda(e);
+                if ((e = cudaEventCreate(&ctx->ev1)) != cudaSuccess) return status_from_cuda(e);
+            }
+            if ((e = cudaEventRecord(ctx->ev0, st)) != cudaSuccess) return status_from_cuda(e);
+        }
+        e = launch_sliding(p, ctx->q, ctx->sm_count, st);
+        if (e == cudaSuccess && ctx->timing) {
+            e = cudaEventRecord(ctx->ev1, st);
+            ctx->ev_pending = true;
+        }
+        if (e != cudaSuccess) return status_from_cuda(e);
+        ctx->launches += 1;
+    }
+    e = launch_finalize(control + 1, results, 1, d_out, st);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    ctx->launches += 1;
+    if (d_D && n > 0) {
+        e = launch_extract(reinterpret_cast<int16_t *>(ws + L.off_drow), n, n, d_D, st);
+        if (e != cudaSuccess) return status_from_cuda(e);
+        ctx->launches += 1;
+    }
+    return FOLD_OK;
+}
+
+// Workspace bytes of a single fold of length n, and where its row-major table and codes sit in it.
+static size_t single_bytes(const fold_ctx *ctx, int n) {
+    if (ctx->method == kSliding) return sliding_layout(n).bytes;
+    return make_plan(&n, 1, ctx->q, ctx->method).bytes;
+}
+static void single_table(const fold_ctx *ctx, int n, uint8_t *ws, const int16_t **drow, int *stride, const uint8_t **codes) {
+    if (ctx->method == kSliding) {
+        const SlidingLayout L = sliding_layout(n);
+        *drow = reinterpret_cast<const int16_t *>(ws + L.off_drow);
+        *stride = n;
+        *codes = ws + L.off_codes;
+        return;
+    }
+    Plan pl = make_plan(&n, 1, ctx->q, ctx->method);
+    *drow = reinterpret_cast<const int16_t *>(ws + pl.off_drow);
+    *stride = pl.sd[0].Np;
+    *codes = ws + pl.off_codes;
+}
+
 int enqueue_single(fold_ctx *ctx, const uint8_t *d_codes, int n, uint8_t *ws, size_t ws_bytes, int32_t *d_out,
                    int16_t *d_D, cudaStream_t st) {
+    if (ctx->method == kSliding) return enqueue_sliding(ctx, d_codes, n, ws, ws_bytes, d_out, d_D, st);
     int32_t len = n;
     Plan pl = make_plan(&len, 1, ctx->q, ctx->method);
     if (ws_bytes < pl.bytes) return FOLD_ENOMEM;
@@ -462,7 +534,9 @@ int fold_set_option(fold_ctx *ctx, int option, int64_t value) {
     if (!ctx) return FOLD_EINVAL;
     switch (option) {
         case FOLD_OPT_METHOD:
-            if (value != FOLD_METHOD_TWO_VECTOR && value != FOLD_METHOD_PLAIN) return FOLD_EINVAL;
+            if (value != FOLD_METHOD_TWO_VECTOR && value != FOLD_METHOD_PLAIN && value != FOLD_METHOD_SLIDING)
+                return FOLD_EINVAL;
+            if (ctx->serve) return FOLD_EAGAIN;   // the serving thread reads the method
             ctx->method = (int)value;
             return FOLD_OK;
         case FOLD_OPT_GRID:
@@ -513,7 +587,7 @@ int fold_get_option(fold_ctx *ctx, int option, int64_t *value) {
         case FOLD_OPT_TIMEOUT_MS: *value = ctx->timeout_ms; return FOLD_OK;
         case FOLD_OPT_KCHUNK: *value = ctx->kc_override; return FOLD_OK;
         case FOLD_OPT_Q: *value = ctx->q; return FOLD_OK;
-        case FOLD_OPT_TILE: *value = tile_of(ctx->q, ctx->method); return FOLD_OK;
+        case FOLD_OPT_TILE: *value = ctx->method == kSliding ? 1 : tile_of(ctx->q, ctx->method); return FOLD_OK;
         case FOLD_OPT_LAUNCHES: *value = (int64_t)ctx->launches; return FOLD_OK;
         case FOLD_OPT_TEST_DROP_TASK: *value = ctx->test_drop_task; return FOLD_OK;
         case FOLD_OPT_TIMING: *value = ctx->timing; return FOLD_OK;
@@ -590,14 +664,13 @@ int fold_rtable(fold_ctx *ctx, uint8_t *out, int64_t cap) {
 }
 
 // Structure workspace: the fold's, then the traceback's stack of pending intervals.
-static size_t structure_bytes(const Plan &pl, int n) {
-    return align_up(pl.bytes, 256) + align_up(sizeof(int2) * (size_t)std::max(n, 1), 256);
+static size_t structure_bytes(size_t fold_bytes, int n) {
+    return align_up(fold_bytes, 256) + align_up(sizeof(int2) * (size_t)std::max(n, 1), 256);
 }
 
 int64_t fold_structure_workspace_bytes(fold_ctx *ctx, int32_t n) {
     if (!ctx || n < 0 || n > FOLD_MAX_N) return -FOLD_EINVAL;
-    Plan pl = make_plan(&n, 1, ctx->q, ctx->method);
-    return (int64_t)structure_bytes(pl, n);
+    return (int64_t)structure_bytes(single_bytes(ctx, n), n);
 }
 
 int fold_structure_dev(fold_ctx *ctx, const uint8_t *d_codes, int32_t n, void *d_ws, int64_t ws_bytes,
@@ -606,17 +679,20 @@ int fold_structure_dev(fold_ctx *ctx, const uint8_t *d_codes, int32_t n, void *d
         return FOLD_EINVAL;
     if ((reinterpret_cast<uintptr_t>(d_ws) & 255) != 0) return FOLD_EINVAL;
     cudaSetDevice(ctx->device);
-    Plan pl = make_plan(&n, 1, ctx->q, ctx->method);
-    if (ws_bytes < 0 || (size_t)ws_bytes < structure_bytes(pl, n)) return FOLD_ENOMEM;
+    const size_t fold_bytes = single_bytes(ctx, n);
+    if (ws_bytes < 0 || (size_t)ws_bytes < structure_bytes(fold_bytes, n)) return FOLD_ENOMEM;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     uint8_t *ws = reinterpret_cast<uint8_t *>(d_ws);
-    int rc = enqueue_single(ctx, d_codes, n, ws, pl.bytes, d_max_pairs, nullptr, st);
+    int rc = enqueue_single(ctx, d_codes, n, ws, fold_bytes, d_max_pairs, nullptr, st);
     if (rc) return rc;
     if (n == 1) return status_from_cuda(cudaMemsetAsync(d_partner, 0xff, sizeof(int32_t), st));
     if (n >= 2) {
-        int2 *stack = reinterpret_cast<int2 *>(ws + align_up(pl.bytes, 256));
-        cudaError_t e = launch_traceback(reinterpret_cast<const int16_t *>(ws + pl.off_drow), pl.sd[0].Np,
-                                         ws + pl.off_codes, n, ctx->pair64, stack, d_partner, d_max_pairs, FOLD_ECUDA, st);
+        int2 *stack = reinterpret_cast<int2 *>(ws + align_up(fold_bytes, 256));
+        const int16_t *drow;
+        const uint8_t *codes;
+        int stride;
+        single_table(ctx, n, ws, &drow, &stride, &codes);
+        cudaError_t e = launch_traceback(drow, stride, codes, n, ctx->pair64, stack, d_partner, d_max_pairs, FOLD_ECUDA, st);
         if (e != cudaSuccess) return status_from_cuda(e);
         ctx->launches += 1;
     }
@@ -634,8 +710,7 @@ int fold_structure(fold_ctx *ctx, const char *seq, int32_t n, int32_t *max_pairs
     int32_t *hres = reinterpret_cast<int32_t *>(hcodes + align_up(nn, 64));
     int32_t *hpart = hres + 16;
     if (!encode_seq(seq, n, hcodes)) return FOLD_EINVAL;
-    Plan pl = make_plan(&n, 1, ctx->q, ctx->method);
-    const size_t wsb = structure_bytes(pl, n);
+    const size_t wsb = structure_bytes(single_bytes(ctx, n), n);
     size_t aux_bytes = align_up(nn, 256) + 256 + align_up(4 * nn, 256);
     if (ensure_buf(ctx->ws, wsb) || ensure_buf(ctx->aux, aux_bytes)) return FOLD_ENOMEM;
     uint8_t *dcodes = reinterpret_cast<uint8_t *>(ctx->aux.ptr);
@@ -663,8 +738,7 @@ int fold_structure(fold_ctx *ctx, const char *seq, int32_t n, int32_t *max_pairs
 
 int64_t fold_workspace_bytes(fold_ctx *ctx, int32_t n) {
     if (!ctx || n < 0 || n > FOLD_MAX_N) return -FOLD_EINVAL;
-    Plan pl = make_plan(&n, 1, ctx->q, ctx->method);
-    return (int64_t)pl.bytes;
+    return (int64_t)single_bytes(ctx, n);
 }
 
 int fold_score_dev(fold_ctx *ctx, const uint8_t *d_codes, int32_t n, void *d_ws, int64_t ws_bytes,
@@ -685,9 +759,8 @@ int fold_score(fold_ctx *ctx, const char *seq, int32_t n, int32_t *max_pairs, in
     uint8_t *hcodes = reinterpret_cast<uint8_t *>(ctx->hstage.ptr);
     int32_t *hres = reinterpret_cast<int32_t *>(hcodes + align_up((size_t)std::max(n, 1), 64));
     if (!encode_seq(seq, n, hcodes)) return FOLD_EINVAL;
-    Plan pl = make_plan(&n, 1, ctx->q, ctx->method);
     size_t aux_bytes = align_up((size_t)std::max(n, 1), 256) + 256;
-    if (ensure_buf(ctx->ws, pl.bytes) || ensure_buf(ctx->aux, aux_bytes)) return FOLD_ENOMEM;
+    if (ensure_buf(ctx->ws, single_bytes(ctx, n)) || ensure_buf(ctx->aux, aux_bytes)) return FOLD_ENOMEM;
     if (D_out && n > 0 && ensure_buf(ctx->dout, (size_t)n * n * 2)) return FOLD_ENOMEM;
     uint8_t *dcodes = reinterpret_cast<uint8_t *>(ctx->aux.ptr);
     int32_t *dres = reinterpret_cast<int32_t *>(dcodes + align_up((size_t)std::max(n, 1), 256));
@@ -711,6 +784,7 @@ int fold_score(fold_ctx *ctx, const char *seq, int32_t n, int32_t *max_pairs, in
 int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int32_t *lens, int32_t *max_pairs_out,
                int16_t *const *D_out) {
     if (!ctx || count < 0 || (count > 0 && (!seqs || !lens || !max_pairs_out))) return FOLD_EINVAL;
+    if (ctx->method == kSliding) return FOLD_EINVAL;   // Section 4's organisation folds one sequence
     if (count == 0) return FOLD_OK;
     for (int k = 0; k < count; ++k)
         if (lens[k] < 0 || lens[k] > FOLD_MAX_N || (lens[k] > 0 && !seqs[k])) return FOLD_EINVAL;

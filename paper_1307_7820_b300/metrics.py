@@ -27,6 +27,12 @@ def splits(n: int) -> int:
     return sum((n - d) * d for d in range(1, n))
 
 
+def lookups_relative(n: int, q: int) -> int:
+    """Table lookups of Section 4's organisation: floor((j-i)/q) groups relative to i for every
+    cell, i.e. the sum over diagonals d of (n - d) * floor(d / q)."""
+    return sum((n - d) * (d // q) for d in range(1, n))
+
+
 def lookups(n: int, q: int) -> int:
     """Number of full groups summed over all cells.
 

@@ -78,3 +78,13 @@ def test_sliding_makes_more_lookups_than_aligned_groups():
         _, nl_rel = oracle.two_vector_sliding(s, q, return_lookups=True)
         _, nl_abs = oracle.two_vector(s, q, return_lookups=True)
         assert nl_rel > nl_abs
+
+
+def test_metrics_relative_lookup_count():
+    """The closed form bench.py reports for Section 4's organisation equals the lookups the
+    oracle of that algorithm makes."""
+    from paper_1307_7820_b300 import metrics
+    rng = np.random.default_rng(9)
+    for n, q in [(0, 8), (1, 8), (17, 4), (100, 8), (257, 8), (300, 9), (129, 3)]:
+        _, nl = oracle.two_vector_sliding(_rand_seq(rng, n), q, return_lookups=True)
+        assert metrics.lookups_relative(n, q) == nl == _lookups(n, q)
