@@ -89,9 +89,14 @@ enum fold_option {
     FOLD_OPT_COLUMNS = 13,    /* with tile-only CTAs: each warp owns one tile column and computes it
                                  bottom-up (needs ceil(n_tiles / v) tile CTAs); -1 = automatic
                                  (default, v = 8), 0 = off, v = 1..8 = on, v columns per tile CTA */
-    FOLD_OPT_BATCH_FLAT = 14  /* fold_batch's middle-block chunks: -1 = automatic / 1 = fixed size
+    FOLD_OPT_BATCH_FLAT = 14, /* fold_batch's middle-block chunks: -1 = automatic / 1 = fixed size
                                  (FOLD_OPT_KCHUNK, default 64 blocks), 0 = the single fold's sizes
                                  (growing from both ends of each range) */
+    FOLD_OPT_R_MEMO = 15      /* Section 3.2's partially memoised variant (two-vector, q <= 9): 1 = each
+                                 CTA starts with an empty R and tabulates the row R[h][*] against every
+                                 column vector the first time one of its warps stages a horizontal
+                                 vector h; 0 = the table precomputed at fold_init (default).  Results
+                                 are identical; FOLD_EINVAL for q = 10, FOLD_EAGAIN while serving. */
 };
 
 /* One record per task of the last traced persistent launch. */

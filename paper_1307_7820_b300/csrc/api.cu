@@ -103,6 +103,7 @@ FoldParams make_params(const fold_ctx *ctx, const Plan &pl, uint8_t *ws, const i
     p.rtab = ctx->d_rpacked;
     p.pair64 = ctx->pair64;
     p.timeout_ns = ctx->timeout_ms * 1000000LL;
+    p.memo = (ctx->r_memo && ctx->method == kTwoVector) ? 1 : 0;
     return p;
 }
 
@@ -575,6 +576,11 @@ int fold_set_option(fold_ctx *ctx, int option, int64_t value) {
             if (value < -1 || value > 1) return FOLD_EINVAL;
             ctx->batch_flat_opt = (int)value;
             return FOLD_OK;
+        case FOLD_OPT_R_MEMO:
+            if (value < 0 || value > 1 || (value == 1 && ctx->q >= 10)) return FOLD_EINVAL;
+            if (ctx->serve) return FOLD_EAGAIN;
+            ctx->r_memo = (int)value;
+            return FOLD_OK;
     }
     return FOLD_EINVAL;
 }
@@ -595,6 +601,7 @@ int fold_get_option(fold_ctx *ctx, int option, int64_t *value) {
         case FOLD_OPT_NEAR_CTAS: *value = ctx->near_ctas_opt; return FOLD_OK;
         case FOLD_OPT_COLUMNS: *value = ctx->columns_opt; return FOLD_OK;
         case FOLD_OPT_BATCH_FLAT: *value = ctx->batch_flat_opt; return FOLD_OK;
+        case FOLD_OPT_R_MEMO: *value = ctx->r_memo; return FOLD_OK;
         case FOLD_OPT_KERNEL_NS: {
             if (!ctx->ev_pending) { *value = 0; return FOLD_OK; }
             float ms = 0.f;

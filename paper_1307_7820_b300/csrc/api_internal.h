@@ -65,7 +65,8 @@ struct fold_ctx {
     int test_drop_task = 0;
     int near_ctas_opt = -1;    // -1 automatic, 0 one shared queue, k > 0 k tile-only CTAs
     int columns_opt = -1;      // -1 automatic, 0 off, v >= 1 column mode with v columns per tile CTA
-    int batch_flat_opt = -1;   // fold_batch chunks: -1 / 1 kc blocks each, 0 geometric sizes
+    int batch_flat_opt = -1;
+    int r_memo = 0;            // FOLD_OPT_R_MEMO: tabulate R rows on first sight (two-vector, q <= 9)   // fold_batch chunks: -1 / 1 kc blocks each, 0 geometric sizes
     // tuned single-fold settings per size bucket (fold_tune / fold_tune_load); used when no option
     // forces a layout or a chunk size
     std::map<int, fold::TuneEntry> tune;

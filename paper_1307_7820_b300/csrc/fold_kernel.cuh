@@ -236,12 +236,23 @@ struct ScratchChecks {
     static constexpr bool ok = true;
 };
 
+// partially memoised R (two-vector, byte tables): one bit per horizontal vector, set once its row
+// is tabulated in this CTA
+template <int Q, int M>
+__host__ __device__ constexpr int memo_words() {
+    return (M == kTwoVector && !Cfg<Q, M>::NIB) ? ((1 << (Q - 1)) + 31) / 32 : 0;
+}
+template <int Q, int M>
+__host__ __device__ constexpr size_t memo_offset() {
+    return (size_t)round_up(Cfg<Q, M>::RBYTES, 128) + (size_t)kWarpsPerCta * sizeof(WarpScratch<Q, M>);
+}
+
 template <int Q, int M>
 __host__ __device__ constexpr size_t smem_bytes_for() {
     static_assert(ScratchChecks<Q, M>::ok, "");
-    static_assert((size_t)round_up(Cfg<Q, M>::RBYTES, 128) + (size_t)kWarpsPerCta * sizeof(WarpScratch<Q, M>) <= 227 * 1024,
+    static_assert(memo_offset<Q, M>() + 16 * (size_t)((memo_words<Q, M>() + 3) / 4) <= 227 * 1024,
                   "R table plus per-warp scratch must fit the 227 KB per-block shared memory of sm_103a");
-    return (size_t)round_up(Cfg<Q, M>::RBYTES, 128) + (size_t)kWarpsPerCta * sizeof(WarpScratch<Q, M>);
+    return memo_offset<Q, M>() + 16 * (size_t)((memo_words<Q, M>() + 3) / 4);
 }
 
 // R lookup: value of R at (h-row byte offset hs, column vector c)
@@ -258,6 +269,47 @@ template <int Q>
 __device__ __forceinline__ int hrow_offset(int h) {
     if constexpr (Q >= 10) return h << (Q - 2);   // nibbles: 2^(q-1) entries = 2^(q-2) bytes per row
     else return h << (Q - 1);
+}
+
+// Partially memoised R (Section 3.2): before a warp stages features for lookups, every row R[h][*]
+// they use must be tabulated in this CTA.  Lanes whose h has no row yet ask; the warp fills the asked
+// rows one at a time (lane l computes the entries c = l, l+32, ... by the Section 3.1 routine, the
+// best prefix sum of h_p - c_p over p), then lane 0 publishes the row's bit with a CTA-scope release;
+// a reader sees the bit with an acquire load before it reads the row.  Two warps may fill the same
+// row at once: they write the same bytes.
+template <int Q, int M>
+__device__ __noinline__ void memo_fill(uint8_t *Rs, unsigned ask_mask, unsigned h, int lane) {
+    constexpr int NB = Q - 1;
+    unsigned *bits = reinterpret_cast<unsigned *>(Rs + memo_offset<Q, M>());
+    unsigned m = ask_mask;
+    while (m) {
+        const unsigned hr = __shfl_sync(FULL, h, __ffs(m) - 1);
+        for (int c = lane; c < (1 << NB); c += 32) {
+            int best = 0, sum = 0;
+#pragma unroll
+            for (int p = 1; p <= NB; ++p) {
+                sum += (int)((hr >> (p - 1)) & 1u) - (int)(((unsigned)c >> (p - 1)) & 1u);
+                best = max(best, sum);
+            }
+            Rs[(hr << NB) | (unsigned)c] = (uint8_t)best;
+        }
+        __syncwarp();
+        if (lane == 0)
+            asm volatile("red.release.cta.shared::cta.or.b32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(bits + (hr >> 5))),
+                         "r"(1u << (hr & 31)) : "memory");
+        m &= ~__ballot_sync(FULL, (m >> lane & 1u) && h == hr);
+    }
+    __syncwarp();
+}
+template <int Q, int M>
+__device__ __forceinline__ void memo_ensure(const FoldParams &P, const uint8_t *Rs, unsigned h, bool need, int lane) {
+    if constexpr (memo_words<Q, M>() > 0) {
+        if (!P.memo) return;
+        const unsigned *bits = reinterpret_cast<const unsigned *>(Rs + memo_offset<Q, M>());
+        const bool ask = need && !((ld_acquire_cta(reinterpret_cast<const int *>(bits + (h >> 5))) >> (h & 31)) & 1);
+        const unsigned m = __ballot_sync(FULL, ask);
+        if (m) memo_fill<Q, M>(const_cast<uint8_t *>(Rs), m, h, lane);
+    }
 }
 
 // One full group's candidate of Eq. 3, A + B + R[h][c], scaled by 2^16 (the low half is not zero):
@@ -323,6 +375,8 @@ __device__ __forceinline__ void far_chunk_tv(const FoldParams &P, const SeqDesc 
         }
 #pragma unroll
         for (int gl = 0; gl < G; ++gl) cb[gl] = cfn[gl];
+#pragma unroll
+        for (int gl = 0; gl < G; ++gl) memo_ensure<Q, kTwoVector>(P, Rs, rfn[gl] & C::BMASK, valid, lane);
 #pragma unroll
         for (int g4 = 0; g4 < WS::GA / 4; ++g4)
             reinterpret_cast<uint4 *>(&ws.rfw[lane][0])[g4] = make_uint4(w[4 * g4], w[4 * g4 + 1], w[4 * g4 + 2], w[4 * g4 + 3]);
@@ -512,6 +566,7 @@ __device__ __forceinline__ void far_strip_tv(const FoldParams &P, const SeqDesc 
             for (int p2 = 0; p2 < S / 2; ++p2)
                 ws.scv[gl][S + p2][lane] = (cfn[2 * p2][gl] >> 16) | (cfn[2 * p2 + 1][gl] & 0xffff0000u);
             ws.rf[gl][lane] = make_int2((int)((rfn[gl] >> 16) * 0x10001u), hrow_offset<Q>((int)(rfn[gl] & C::BMASK)));
+            memo_ensure<Q, kTwoVector>(P, Rs, rfn[gl] & C::BMASK, lv, lane);
         }
         if (K < Kb) {   // prefetch the next block
 #pragma unroll
@@ -830,6 +885,8 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int idx = e * 32 + lane;
+                memo_ensure<Q, M>(P, Rs, fv[e] & C::BMASK, idx < T * G, lane);
+                memo_ensure<Q, M>(P, Rs, fb[e] & C::BMASK, idx < T * G && lateB, lane);
                 if (idx < T * G) {
                     // the row's word for group gl: A, or -32768 while the group is not complete
                     // below the row (gl*q <= row), and the R-row offset of h
@@ -990,6 +1047,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int idx = e * 32 + lane;
+            memo_ensure<Q, M>(P, Rs, fa[e] & C::BMASK, idx < T * G && lateA, lane);
             if (idx < T * G) ws.lrf[0][idx / G][idx % G] = group_word<Q>(fa[e]);
         }
     } else {
@@ -1380,11 +1438,19 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
     using C = Cfg<Q, M>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint8_t *Rs = smem;
+    if constexpr (memo_words<Q, M>() > 0) {
+        // memoised R: no table yet, no row tabulated
+        if (P.memo) {
+            unsigned *bits = reinterpret_cast<unsigned *>(smem + memo_offset<Q, M>());
+            for (int v = threadIdx.x; v < memo_words<Q, M>(); v += blockDim.x) bits[v] = 0u;
+        }
+    }
     if constexpr (C::RBYTES > 0) {
         const uint4 *src = reinterpret_cast<const uint4 *>(P.rtab);
         uint4 *dst = reinterpret_cast<uint4 *>(smem);
         // the device copy of R is padded to a multiple of 256 bytes, so rounding up stays in bounds
-        for (int v = threadIdx.x; v < (C::RBYTES + 15) / 16; v += blockDim.x) dst[v] = __ldg(src + v);
+        if (!P.memo)
+            for (int v = threadIdx.x; v < (C::RBYTES + 15) / 16; v += blockDim.x) dst[v] = __ldg(src + v);
     }
     WarpScratch<Q, M> *wsb = reinterpret_cast<WarpScratch<Q, M> *>(smem + round_up(C::RBYTES, 128));
     WarpScratch<Q, M> &ws = wsb[warp];

@@ -254,6 +254,7 @@ static void serve_loop(ServeState *S) {
         p.results = reinterpret_cast<int *>(d + o_res);
         p.rtab = ctx->d_rpacked;
         p.pair64 = ctx->pair64;
+        p.memo = (ctx->r_memo && ctx->method == kTwoVector) ? 1 : 0;
         p.timeout_ns = ctx->timeout_ms * 1000000LL;
         p.trace = nullptr;
         const auto t_launch = std::chrono::steady_clock::now();
