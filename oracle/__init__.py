@@ -14,6 +14,7 @@ Functions (each cites the passage of the paper it follows; see ``oracle.c``):
 * :func:`two_vector`    -- Section 3.1, Algorithm 1 (serial two-vector).
 * :func:`two_vector_sliding` -- Section 4, the parallel two-vector algorithm with
   difference vectors at every cell and groups relative to i.
+* :func:`fg`            -- Section 3.2, the FG algorithm (a table per row and group).
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against brute force, hand-worked fixtures in ``tests/golden/``, closed forms
@@ -79,6 +80,8 @@ def _load():
         lib.oracle_two_vector.restype = ctypes.c_int
         lib.oracle_two_vector_sliding.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_uint16, i32p, i64p]
         lib.oracle_two_vector_sliding.restype = ctypes.c_int
+        lib.oracle_fg.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_uint16, i32p, i64p, i64p]
+        lib.oracle_fg.restype = ctypes.c_int
         lib.oracle_traceback.argtypes = [u8p, ctypes.c_int, ctypes.c_uint16, i32p, i32p]
         lib.oracle_traceback.restype = ctypes.c_int
         _lib = lib
@@ -191,3 +194,18 @@ def two_vector_sliding(seq: str, q: int, mask: int = MASK6, return_lookups: bool
         if rc != 0:
             raise MemoryError("oracle_two_vector_sliding failed")
     return (D, int(nl.value)) if return_lookups else D
+
+
+def fg(seq: str, q: int, mask: int = MASK6, return_counts: bool = False):
+    """Full table by the FG algorithm (int32); optionally (lookups, row-group tables built)."""
+    lib = _load()
+    c = encode(seq)
+    n = len(c)
+    D = np.zeros((n, n), dtype=np.int32)
+    nl, nt = ctypes.c_int64(0), ctypes.c_int64(0)
+    if n:
+        rc = lib.oracle_fg(_u8(c), n, q, mask, D.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(nl),
+                           ctypes.byref(nt))
+        if rc != 0:
+            raise MemoryError("oracle_fg failed")
+    return (D, int(nl.value), int(nt.value)) if return_counts else D

@@ -26,6 +26,10 @@
  *                       difference vectors at every cell and groups relative
  *                       to i, filled diagonal by diagonal, one column per
  *                       process.
+ *   oracle_fg           Section 3.2, the FG algorithm: Algorithm 1's fill with
+ *                       a table per row and group (D(i,gq) folded in) built
+ *                       when the group completes, instead of one table over
+ *                       vector pairs.
  *   oracle_traceback    Section 2, the traceback: the argmax of Eq. 1 (D*)
  *                       re-evaluated at each visited cell of a finished table,
  *                       giving one optimal set of pairs.
@@ -341,6 +345,96 @@ int oracle_two_vector_sliding(const uint8_t *codes, int n, int q, uint16_t mask,
     free(R);
     free(dh);
     free(dv);
+    return 0;
+}
+
+/* Section 3.2, the FG algorithm (Frid and Gusfield).  The fill and the
+ * groups are Algorithm 1's (column by column; group g full for cell (i,j) iff
+ * g*q >= i and g*q+q <= j; the residual loops before the first and after the
+ * last full group), but there is no table over vector pairs: when row i's
+ * group g is complete (D(i, g*q+q-1) is known), the preprocessing routine runs
+ * for that row's own horizontal vector h against every vertical vector c,
+ * D(i, g*q) is added, and the result is tabled per row and group:
+ *   FG[i][g][c] = D(i, g*q) + max_{0<=k<=q-1} sum_{p<=k} (h_p - c_p).
+ * A cell's group term is FG[i][g][c(g,j)] + D(g*q+1, j).  The text's "added to
+ * D(q,j)" is read as D(g*q+1, j), the top of the group's column segment (as
+ * in Eq. 3).  If lookups is not NULL it receives the number of table lookups;
+ * if tables is not NULL, the number of (row, group) tables built.  D as in
+ * oracle_nussinov. */
+int oracle_fg(const uint8_t *codes, int n, int q, uint16_t mask, int32_t *D, int64_t *lookups, int64_t *tables) {
+    if (n < 0 || q < 1 || q > 12) return -1;
+    if (lookups) *lookups = 0;
+    if (tables) *tables = 0;
+    if (n == 0) return 0;
+    const int nb = q - 1, nc = 1 << nb, ng = n / q + 2;
+    int32_t *fg = (int32_t *)calloc((size_t)n * ng * nc, sizeof(int32_t));
+    uint32_t *cv = (uint32_t *)calloc((size_t)n * ng, sizeof(uint32_t));
+    if (!fg || !cv) { free(fg); free(cv); return -2; }
+    memset(D, 0, sizeof(int32_t) * (size_t)n * (size_t)n);
+#define DD(a, b) D[(size_t)(a) * n + (b)]
+    int64_t nl = 0, nt = 0;
+    for (int j = 0; j < n; ++j) {
+        /* i = j: the diagonal cell, D(j,j) = 0, only completes a group when q = 1 */
+        for (int i = j; i >= 0; --i) {
+            if (i < j) {
+                int inner = (i + 1 <= j - 1) ? DD(i + 1, j - 1) : 0;
+                int best = pair_b(mask, codes[i], codes[j]) + inner;
+                int gfirst = (i + q - 1) / q;
+                int glast = j >= q ? (j - q) / q : -1;
+                if (gfirst <= glast) {
+                    for (int k = i + 1; k <= gfirst * q; ++k) {
+                        int v = DD(i, k - 1) + DD(k, j);
+                        if (v > best) best = v;
+                    }
+                    for (int k = glast * q + q + 1; k <= j; ++k) {
+                        int v = DD(i, k - 1) + DD(k, j);
+                        if (v > best) best = v;
+                    }
+                    for (int g = gfirst; g <= glast; ++g) {
+                        int v = fg[((size_t)i * ng + g) * nc + cv[(size_t)j * ng + g]] + DD(g * q + 1, j);
+                        ++nl;
+                        if (v > best) best = v;
+                    }
+                } else {
+                    for (int k = i + 1; k <= j; ++k) {
+                        int v = DD(i, k - 1) + DD(k, j);
+                        if (v > best) best = v;
+                    }
+                }
+                DD(i, j) = best;
+            }
+            /* vertical vector of column j, group g, complete once D(g*q+1, j) is known (as in Algorithm 1) */
+            if (i >= 1 && (i - 1) % q == 0) {
+                int g = (i - 1) / q;
+                if (g * q + q <= j) {
+                    uint32_t c = 0;
+                    for (int p = 1; p <= q - 1; ++p)
+                        c |= (uint32_t)(DD(g * q + p, j) - DD(g * q + p + 1, j)) << (p - 1);
+                    cv[(size_t)j * ng + g] = c;
+                }
+            }
+            /* row i's group g complete: run the preprocessing for its vector against every c */
+            if ((j + 1) % q == 0) {
+                int g = (j + 1) / q - 1;
+                if (g * q >= i) {
+                    uint32_t h = 0;
+                    for (int p = 1; p <= q - 1; ++p)
+                        h |= (uint32_t)(DD(i, g * q + p) - DD(i, g * q + p - 1)) << (p - 1);
+                    for (int c = 0; c < nc; ++c) {
+                        int mv, mi;
+                        preprocess_pair(q, h, (unsigned)c, &mv, &mi);
+                        fg[((size_t)i * ng + g) * nc + c] = DD(i, g * q) + mv;
+                    }
+                    ++nt;
+                }
+            }
+        }
+    }
+#undef DD
+    if (lookups) *lookups = nl;
+    if (tables) *tables = nt;
+    free(fg);
+    free(cv);
     return 0;
 }
 
