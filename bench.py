@@ -400,6 +400,24 @@ def main():
                 "note": "Section 3.2 partially memoised: each CTA tabulates R[h][*] the first time it stages h"}
         mf.close()
 
+    # ---- Section 3.2's FG algorithm (a table per row and group), per-column kernel, same input
+    fgr = None
+    if not a.no_sliding:
+        fgr = {}
+        for fq in (3, 8):
+            ff = fold.Folder(q=fq, method="fg", device=local)
+            ff.option(fold.FOLD_OPT_TIMING, 1)
+            r_f = device_run(ff, 3, 1)
+            assert r_f["max_pairs"] == r_tv["max_pairs"], "FG and two-vector disagree"
+            f_ms = statistics.mean(r_f["step_ms"])
+            fgr[f"q{fq}"] = {"ms_per_step": f_ms, "cells_per_s": cells / (f_ms * 1e-3),
+                             "kernel_ms": statistics.mean(r_f["kern_ms"]),
+                             "row_group_tables": metrics.fg_tables(n, fq),
+                             "tiled_speedup": f_ms / statistics.mean(r_tv["step_ms"])}
+            ff.close()
+        fgr["note"] = ("Section 3.2 FG: Algorithm 1's groups, a table per row and group built when the group "
+                       "completes; one warp per column like 'sliding'")
+
     # ---- Section 4's organisation as printed (one warp per column, per-cell vectors), same input
     sliding = None
     if not a.no_sliding:
@@ -569,6 +587,7 @@ def main():
                   "kernel_ms": statistics.mean(r_pl["kern_ms"])},
         "memoized": memo,
         "sliding": sliding,
+        "fg": fgr,
         "batch": batch, "serve": serve, "q_sweep": qsweep, "cpu_two_vector": cpu_tv, "structure": structure,
         "max_pairs": r_tv["max_pairs"],
     }

@@ -62,12 +62,19 @@ enum fold_status {
 enum fold_method {
     FOLD_METHOD_TWO_VECTOR = 0, /* Section 3.1 / Section 4: R-table lookups per group of q splits */
     FOLD_METHOD_PLAIN = 1,      /* Section 2 / Section 4: every split evaluated (comparison kernel) */
-    FOLD_METHOD_SLIDING = 2     /* Section 4 as printed: one warp per column filling it bottom to top,
+    FOLD_METHOD_SLIDING = 2,    /* Section 4 as printed: one warp per column filling it bottom to top,
                                    groups of q splits relative to i and difference vectors stored at
                                    every cell (a second kernel organisation, kept for comparison).
                                    Single folds only (fold_score, fold_score_dev, fold_structure*);
                                    fold_batch, serving and the autotuner return FOLD_EINVAL.  Its
                                    workspace holds D plus two n*n uint32 vector tables (10*n^2 bytes). */
+    FOLD_METHOD_FG = 3          /* Section 3.2's FG algorithm (Frid and Gusfield): Algorithm 1's groups,
+                                   but a table per row and group, FG[i][g][c] = D(i,gq) + the best
+                                   prefix of that row's vector against column vector c, built when the
+                                   group completes (a comparison kernel in the per-column organisation).
+                                   Single folds only, as FOLD_METHOD_SLIDING.  Its workspace holds D,
+                                   the column vectors and n*(n/q+1)*2^(q-1) int16 table entries
+                                   (about 1.2 GB at n = 6000, q = 8; 96 MB at q = 3). */
 };
 
 enum fold_option {

@@ -16,6 +16,7 @@
 #include "fold_common.h"
 #include "kernels.h"
 #include "schedule.h"
+#include "fg.h"
 #include "sliding.h"
 
 using namespace fold;
@@ -389,14 +390,73 @@ static int enqueue_sliding(fold_ctx *ctx, const uint8_t *d_codes, int n, uint8_t
     return FOLD_OK;
 }
 
+// Section 3.2's FG algorithm (FOLD_METHOD_FG): its own workspace layout and kernel.
+static int enqueue_fg(fold_ctx *ctx, const uint8_t *d_codes, int n, uint8_t *ws, size_t ws_bytes, int32_t *d_out,
+                      int16_t *d_D, cudaStream_t st) {
+    const FgLayout L = fg_layout(n, ctx->q);
+    if (ws_bytes < L.bytes) return FOLD_ENOMEM;
+    cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_bytes, st);
+    if (e == cudaSuccess && n > 0) e = cudaMemsetAsync(ws + L.off_drow, 0, (size_t)n * n * 2, st);
+    if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(ws + L.off_codes, d_codes, (size_t)n, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    int *control = reinterpret_cast<int *>(ws + L.off_control);
+    int *results = reinterpret_cast<int *>(ws + L.off_results);
+    if (n >= 2) {
+        FgParams p;
+        p.codes = ws + L.off_codes;
+        p.n = n;
+        p.ng = L.ng;
+        p.drow = reinterpret_cast<int16_t *>(ws + L.off_drow);
+        p.cv = reinterpret_cast<uint32_t *>(ws + L.off_cv);
+        p.fgt = reinterpret_cast<int16_t *>(ws + L.off_fgt);
+        p.progress = reinterpret_cast<int *>(ws + L.off_progress);
+        p.next_col = control;
+        p.error = control + 1;
+        p.result = results;
+        p.pair64 = ctx->pair64;
+        p.timeout_ns = ctx->timeout_ms * 1000000LL;
+        if (ctx->timing) {
+            if (!ctx->ev0) {
+                if ((e = cudaEventCreate(&ctx->ev0)) != cudaSuccess) return status_from_cuda(e);
+                if ((e = cudaEventCreate(&ctx->ev1)) != cudaSuccess) return status_from_cuda(e);
+            }
+            if ((e = cudaEventRecord(ctx->ev0, st)) != cudaSuccess) return status_from_cuda(e);
+        }
+        e = launch_fg(p, ctx->q, ctx->sm_count, st);
+        if (e == cudaSuccess && ctx->timing) {
+            e = cudaEventRecord(ctx->ev1, st);
+            ctx->ev_pending = true;
+        }
+        if (e != cudaSuccess) return status_from_cuda(e);
+        ctx->launches += 1;
+    }
+    e = launch_finalize(control + 1, results, 1, d_out, st);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    ctx->launches += 1;
+    if (d_D && n > 0) {
+        e = launch_extract(reinterpret_cast<int16_t *>(ws + L.off_drow), n, n, d_D, st);
+        if (e != cudaSuccess) return status_from_cuda(e);
+        ctx->launches += 1;
+    }
+    return FOLD_OK;
+}
+
 // Workspace bytes of a single fold of length n, and where its row-major table and codes sit in it.
 static size_t single_bytes(const fold_ctx *ctx, int n) {
     if (ctx->method == kSliding) return sliding_layout(n).bytes;
+    if (ctx->method == kFg) return fg_layout(n, ctx->q).bytes;
     return make_plan(&n, 1, ctx->q, ctx->method).bytes;
 }
 static void single_table(const fold_ctx *ctx, int n, uint8_t *ws, const int16_t **drow, int *stride, const uint8_t **codes) {
     if (ctx->method == kSliding) {
         const SlidingLayout L = sliding_layout(n);
+        *drow = reinterpret_cast<const int16_t *>(ws + L.off_drow);
+        *stride = n;
+        *codes = ws + L.off_codes;
+        return;
+    }
+    if (ctx->method == kFg) {
+        const FgLayout L = fg_layout(n, ctx->q);
         *drow = reinterpret_cast<const int16_t *>(ws + L.off_drow);
         *stride = n;
         *codes = ws + L.off_codes;
@@ -411,6 +471,7 @@ static void single_table(const fold_ctx *ctx, int n, uint8_t *ws, const int16_t 
 int enqueue_single(fold_ctx *ctx, const uint8_t *d_codes, int n, uint8_t *ws, size_t ws_bytes, int32_t *d_out,
                    int16_t *d_D, cudaStream_t st) {
     if (ctx->method == kSliding) return enqueue_sliding(ctx, d_codes, n, ws, ws_bytes, d_out, d_D, st);
+    if (ctx->method == kFg) return enqueue_fg(ctx, d_codes, n, ws, ws_bytes, d_out, d_D, st);
     int32_t len = n;
     Plan pl = make_plan(&len, 1, ctx->q, ctx->method);
     if (ws_bytes < pl.bytes) return FOLD_ENOMEM;
@@ -535,7 +596,8 @@ int fold_set_option(fold_ctx *ctx, int option, int64_t value) {
     if (!ctx) return FOLD_EINVAL;
     switch (option) {
         case FOLD_OPT_METHOD:
-            if (value != FOLD_METHOD_TWO_VECTOR && value != FOLD_METHOD_PLAIN && value != FOLD_METHOD_SLIDING)
+            if (value != FOLD_METHOD_TWO_VECTOR && value != FOLD_METHOD_PLAIN && value != FOLD_METHOD_SLIDING &&
+                value != FOLD_METHOD_FG)
                 return FOLD_EINVAL;
             if (ctx->serve) return FOLD_EAGAIN;   // the serving thread reads the method
             ctx->method = (int)value;
@@ -593,7 +655,7 @@ int fold_get_option(fold_ctx *ctx, int option, int64_t *value) {
         case FOLD_OPT_TIMEOUT_MS: *value = ctx->timeout_ms; return FOLD_OK;
         case FOLD_OPT_KCHUNK: *value = ctx->kc_override; return FOLD_OK;
         case FOLD_OPT_Q: *value = ctx->q; return FOLD_OK;
-        case FOLD_OPT_TILE: *value = ctx->method == kSliding ? 1 : tile_of(ctx->q, ctx->method); return FOLD_OK;
+        case FOLD_OPT_TILE: *value = ctx->method >= kSliding ? 1 : tile_of(ctx->q, ctx->method); return FOLD_OK;
         case FOLD_OPT_LAUNCHES: *value = (int64_t)ctx->launches; return FOLD_OK;
         case FOLD_OPT_TEST_DROP_TASK: *value = ctx->test_drop_task; return FOLD_OK;
         case FOLD_OPT_TIMING: *value = ctx->timing; return FOLD_OK;
@@ -791,7 +853,7 @@ int fold_score(fold_ctx *ctx, const char *seq, int32_t n, int32_t *max_pairs, in
 int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int32_t *lens, int32_t *max_pairs_out,
                int16_t *const *D_out) {
     if (!ctx || count < 0 || (count > 0 && (!seqs || !lens || !max_pairs_out))) return FOLD_EINVAL;
-    if (ctx->method == kSliding) return FOLD_EINVAL;   // Section 4's organisation folds one sequence
+    if (ctx->method >= kSliding) return FOLD_EINVAL;   // the per-column comparison kernels fold one sequence
     if (count == 0) return FOLD_OK;
     for (int k = 0; k < count; ++k)
         if (lens[k] < 0 || lens[k] > FOLD_MAX_N || (lens[k] > 0 && !seqs[k])) return FOLD_EINVAL;

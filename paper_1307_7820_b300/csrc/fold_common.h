@@ -19,8 +19,9 @@ constexpr int kNeg16 = -32768;                  // int16 "minus infinity" for th
 constexpr int kPadCode = 4;                     // padding base: pairs with nothing
 constexpr int kTraceWords = 10;                 // 64-bit words per task trace record
 
-// kSliding: Section 4's organisation with per-cell vectors (its own kernel, single folds only)
-enum Method : int { kTwoVector = 0, kPlain = 1, kSliding = 2 };
+// kSliding: Section 4's organisation with per-cell vectors; kFg: Section 3.2's FG algorithm (each its
+// own per-column kernel, single folds only)
+enum Method : int { kTwoVector = 0, kPlain = 1, kSliding = 2, kFg = 3 };
 enum TaskType : int { kTaskNear = 0, kTaskFar = 1, kTaskFarStrip = 2 };
 
 // tile edge for a given q (two-vector) or the plain kernel

@@ -315,7 +315,7 @@ extern "C" {
 
 int fold_serve_start(fold_ctx *ctx, int64_t budget_bytes, int32_t max_inflight) {
     if (!ctx || budget_bytes < (1 << 20) || max_inflight < 1) return FOLD_EINVAL;
-    if (ctx->serve || ctx->method == kSliding) return FOLD_EINVAL;
+    if (ctx->serve || ctx->method >= kSliding) return FOLD_EINVAL;
     cudaSetDevice(ctx->device);
     ServeState *S = new ServeState();
     S->ctx = ctx;
@@ -425,7 +425,7 @@ int fold_serve_poll(fold_ctx *ctx, uint64_t ticket, int32_t *max_pairs, int16_t 
 }
 
 int fold_serve_warm(fold_ctx *ctx, int32_t max_n) {
-    if (!ctx || max_n < 0 || max_n > FOLD_MAX_N || ctx->method == kSliding) return FOLD_EINVAL;
+    if (!ctx || max_n < 0 || max_n > FOLD_MAX_N || ctx->method >= kSliding) return FOLD_EINVAL;
     if (max_n == 0) return FOLD_OK;
     int n = max_n;
     const int NTmax = make_plan(&n, 1, ctx->q, ctx->method).NTs[0];

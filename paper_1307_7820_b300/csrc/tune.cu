@@ -72,7 +72,7 @@ using namespace fold;
 extern "C" {
 
 int fold_tune(fold_ctx *ctx, int32_t n, int32_t reps, fold_tune_result *out) {
-    if (!ctx || !out || n < 1 || n > FOLD_MAX_N || reps < 1 || reps > 100 || ctx->method == kSliding) return FOLD_EINVAL;
+    if (!ctx || !out || n < 1 || n > FOLD_MAX_N || reps < 1 || reps > 100 || ctx->method >= kSliding) return FOLD_EINVAL;
     if (ctx->serve) return FOLD_EAGAIN;   // the serving thread owns the context's stream
     cudaSetDevice(ctx->device);
     memset(out, 0, sizeof *out);

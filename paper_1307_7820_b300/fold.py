@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfold_b300.so")
 
 FOLD_OK, FOLD_EINVAL, FOLD_ENOMEM, FOLD_EAGAIN, FOLD_ETIMEOUT, FOLD_ECUDA, FOLD_ENOTREADY = range(7)
-FOLD_METHOD_TWO_VECTOR, FOLD_METHOD_PLAIN, FOLD_METHOD_SLIDING = 0, 1, 2
+FOLD_METHOD_TWO_VECTOR, FOLD_METHOD_PLAIN, FOLD_METHOD_SLIDING, FOLD_METHOD_FG = 0, 1, 2, 3
 FOLD_OPT_METHOD, FOLD_OPT_GRID, FOLD_OPT_TIMEOUT_MS, FOLD_OPT_KCHUNK = 1, 2, 3, 4
 FOLD_OPT_Q, FOLD_OPT_TILE, FOLD_OPT_LAUNCHES, FOLD_OPT_TEST_DROP_TASK = 5, 6, 7, 8
 FOLD_OPT_TIMING, FOLD_OPT_KERNEL_NS, FOLD_OPT_TRACE, FOLD_OPT_NEAR_CTAS, FOLD_OPT_COLUMNS = 9, 10, 11, 12, 13
@@ -327,7 +327,7 @@ class Folder:
     def set_method(self, method: str) -> None:
         fold_set_option(self.ctx, FOLD_OPT_METHOD,
                         {"two_vector": FOLD_METHOD_TWO_VECTOR, "plain": FOLD_METHOD_PLAIN,
-                         "sliding": FOLD_METHOD_SLIDING}[method])
+                         "sliding": FOLD_METHOD_SLIDING, "fg": FOLD_METHOD_FG}[method])
 
     @property
     def q(self) -> int:

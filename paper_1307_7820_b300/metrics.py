@@ -33,6 +33,12 @@ def lookups_relative(n: int, q: int) -> int:
     return sum((n - d) * (d // q) for d in range(1, n))
 
 
+def fg_tables(n: int, q: int) -> int:
+    """Row-group tables the FG algorithm builds: row i's group g is complete (and tabulated) when
+    D(i, g*q+q-1) exists, for every row i <= g*q."""
+    return sum(g * q + 1 for g in range(n // q + 1) if g * q + q - 1 <= n - 1)
+
+
 def lookups(n: int, q: int) -> int:
     """Number of full groups summed over all cells.
 

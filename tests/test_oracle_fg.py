@@ -72,3 +72,11 @@ def test_fg_same_lookups_as_algorithm1():
         _, nl_fg, nt = oracle.fg(s, q, return_counts=True)
         _, nl_tv = oracle.two_vector(s, q, return_lookups=True)
         assert nl_fg == nl_tv and nt > 0
+
+
+def test_metrics_fg_table_count():
+    from paper_1307_7820_b300 import metrics
+    rng = np.random.default_rng(4)
+    for n, q in [(0, 3), (1, 3), (17, 4), (100, 3), (131, 8)]:
+        _, _, nt = oracle.fg(_rand_seq(rng, n), q, return_counts=True)
+        assert metrics.fg_tables(n, q) == nt == _tables(n, q)
