@@ -77,9 +77,10 @@ struct FoldParams {
     // tasks[0, nnear) still lists them (diagonal by diagonal) for their chunk counts.
     int col_mode;
     int cols_per_cta;
-    // two-vector, q <= 9: R starts empty in each CTA and a row R[h][*] is tabulated against every
-    // column vector the first time a warp of the CTA stages a feature with horizontal vector h
-    // (Section 3.2's partially memoised variant); 0: the precomputed table is copied in
+    // two-vector, q <= 9: launch the kernel instantiation in which R starts empty in each CTA and a
+    // row R[h][*] is tabulated against every column vector the first time a warp of the CTA stages a
+    // feature with horizontal vector h (Section 3.2's partially memoised variant); 0: the one that
+    // copies the precomputed table in
     int memo;
     int *error;               // first error code (0 = none) and where
     const SeqDesc *seqs;

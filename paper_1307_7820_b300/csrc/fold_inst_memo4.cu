@@ -1,0 +1,7 @@
+// fold_inst_memo4.cu -- instantiation of the persistent fold kernel, two-vector with the partially
+// memoised table of Section 3.2 (q = 4).
+#include "fold_kernel.cuh"
+
+namespace fold {
+cudaError_t launch_memo4(const FoldParams &p, int grid, cudaStream_t st) { return launch_q<4, kTwoVector, true>(p, grid, st); }
+}  // namespace fold

@@ -26,6 +26,14 @@ FOLD_INST_DECL(tv8)
 FOLD_INST_DECL(tv9)
 FOLD_INST_DECL(tv10)
 FOLD_INST_DECL(plain)
+cudaError_t launch_memo2(const FoldParams &p, int grid, cudaStream_t st);
+cudaError_t launch_memo3(const FoldParams &p, int grid, cudaStream_t st);
+cudaError_t launch_memo4(const FoldParams &p, int grid, cudaStream_t st);
+cudaError_t launch_memo5(const FoldParams &p, int grid, cudaStream_t st);
+cudaError_t launch_memo6(const FoldParams &p, int grid, cudaStream_t st);
+cudaError_t launch_memo7(const FoldParams &p, int grid, cudaStream_t st);
+cudaError_t launch_memo8(const FoldParams &p, int grid, cudaStream_t st);
+cudaError_t launch_memo9(const FoldParams &p, int grid, cudaStream_t st);
 
 // ------------------------------------------------------------------ R table
 // R[(h << (q-1)) | c] = max over k in [0,q-1] of sum_{p<=k} (h_p - c_p), with
@@ -225,6 +233,19 @@ cudaError_t launch_finalize(const int *error, const int *results, int count, int
 
 cudaError_t launch_fold(const FoldParams &p, int q, int method, int grid, cudaStream_t st) {
     if (method == kPlain) return launch_plain(p, grid, st);
+    if (p.memo) {   // Section 3.2's partially memoised table (same shared memory and occupancy)
+        switch (q) {
+            case 2: return launch_memo2(p, grid, st);
+            case 3: return launch_memo3(p, grid, st);
+            case 4: return launch_memo4(p, grid, st);
+            case 5: return launch_memo5(p, grid, st);
+            case 6: return launch_memo6(p, grid, st);
+            case 7: return launch_memo7(p, grid, st);
+            case 8: return launch_memo8(p, grid, st);
+            case 9: return launch_memo9(p, grid, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (q) {
         case 2: return launch_tv2(p, grid, st);
         case 3: return launch_tv3(p, grid, st);

@@ -301,10 +301,9 @@ __device__ __noinline__ void memo_fill(uint8_t *Rs, unsigned ask_mask, unsigned 
     }
     __syncwarp();
 }
-template <int Q, int M>
-__device__ __forceinline__ void memo_ensure(const FoldParams &P, const uint8_t *Rs, unsigned h, bool need, int lane) {
-    if constexpr (memo_words<Q, M>() > 0) {
-        if (!P.memo) return;
+template <int Q, int M, bool MEMO>
+__device__ __forceinline__ void memo_ensure(const uint8_t *Rs, unsigned h, bool need, int lane) {
+    if constexpr (MEMO && memo_words<Q, M>() > 0) {
         const unsigned *bits = reinterpret_cast<const unsigned *>(Rs + memo_offset<Q, M>());
         const bool ask = need && !((ld_acquire_cta(reinterpret_cast<const int *>(bits + (h >> 5))) >> (h & 31)) & 1);
         const unsigned m = __ballot_sync(FULL, ask);
@@ -346,7 +345,7 @@ __device__ __forceinline__ uint32_t group_word(uint32_t f) {
 // broadcast load; the lane's column feature (B << 16 | c) is used as loaded.  The features of
 // block K+1 are loaded while block K is evaluated, so each block's L2 latency overlaps the
 // previous block.  m[] is kept scaled by 2^16 inside (see group_term).
-template <int Q>
+template <int Q, bool MEMO>
 __device__ __forceinline__ void far_chunk_tv(const FoldParams &P, const SeqDesc &sd, int I, int J, int Ka, int Kb,
                                              int *m, WarpScratch<Q, kTwoVector> &ws, const uint8_t *Rs, int lane) {
     using C = Cfg<Q, kTwoVector>;
@@ -376,7 +375,7 @@ __device__ __forceinline__ void far_chunk_tv(const FoldParams &P, const SeqDesc 
 #pragma unroll
         for (int gl = 0; gl < G; ++gl) cb[gl] = cfn[gl];
 #pragma unroll
-        for (int gl = 0; gl < G; ++gl) memo_ensure<Q, kTwoVector>(P, Rs, rfn[gl] & C::BMASK, valid, lane);
+        for (int gl = 0; gl < G; ++gl) memo_ensure<Q, kTwoVector, MEMO>(Rs, rfn[gl] & C::BMASK, valid, lane);
 #pragma unroll
         for (int g4 = 0; g4 < WS::GA / 4; ++g4)
             reinterpret_cast<uint4 *>(&ws.rfw[lane][0])[g4] = make_uint4(w[4 * g4], w[4 * g4 + 1], w[4 * g4 + 2], w[4 * g4 + 3]);
@@ -491,7 +490,7 @@ struct NextTask {
 };
 
 // ---------------------------------------------------------------- FAR task
-template <int Q, int M>
+template <int Q, int M, bool MEMO>
 __device__ __forceinline__ long long run_far(const FoldParams &P, const SeqDesc &sd, int I, int J, int Ka, int Kb,
                         WarpScratch<Q, M> &ws, const uint8_t *Rs, int lane, long long *tdeps, NextTask &nt) {
     constexpr int T = Cfg<Q, M>::T;
@@ -509,7 +508,7 @@ __device__ __forceinline__ long long run_far(const FoldParams &P, const SeqDesc 
     if constexpr (M == kTwoVector) {
 #pragma unroll
         for (int r = 0; r < T; ++r) m[r] = 0;
-        far_chunk_tv<Q>(P, sd, I, J, Ka, Kb, m, ws, Rs, lane);
+        far_chunk_tv<Q, MEMO>(P, sd, I, J, Ka, Kb, m, ws, Rs, lane);
     } else {
         unsigned mp[T];
 #pragma unroll
@@ -539,7 +538,7 @@ __device__ __forceinline__ long long run_far(const FoldParams &P, const SeqDesc 
 // 16-bit halves, h-row offset) is one broadcast load that serves S lookups;
 // two columns share one packed 16x2 accumulator (A + B + R <= n/2 < 2^15, so
 // the halves never carry into each other).
-template <int Q, int S>
+template <int Q, int S, bool MEMO>
 __device__ __forceinline__ void far_strip_tv(const FoldParams &P, const SeqDesc &sd, int I, int J0, int Seff, int Ka,
                                              int Kb, unsigned (&m2)[S / 2][Cfg<Q, kTwoVector>::T],
                                              WarpScratch<Q, kTwoVector> &ws, const uint8_t *Rs, int lane) {
@@ -566,7 +565,7 @@ __device__ __forceinline__ void far_strip_tv(const FoldParams &P, const SeqDesc 
             for (int p2 = 0; p2 < S / 2; ++p2)
                 ws.scv[gl][S + p2][lane] = (cfn[2 * p2][gl] >> 16) | (cfn[2 * p2 + 1][gl] & 0xffff0000u);
             ws.rf[gl][lane] = make_int2((int)((rfn[gl] >> 16) * 0x10001u), hrow_offset<Q>((int)(rfn[gl] & C::BMASK)));
-            memo_ensure<Q, kTwoVector>(P, Rs, rfn[gl] & C::BMASK, lv, lane);
+            memo_ensure<Q, kTwoVector, MEMO>(Rs, rfn[gl] & C::BMASK, lv, lane);
         }
         if (K < Kb) {   // prefetch the next block
 #pragma unroll
@@ -667,7 +666,7 @@ __device__ __forceinline__ void far_strip_plain(const FoldParams &P, const SeqDe
     }
 }
 
-template <int Q, int M>
+template <int Q, int M, bool MEMO>
 __device__ __forceinline__ long long run_far_strip(const FoldParams &P, const SeqDesc &sd, int I, int J0, int Ka,
                                                    int Kb, WarpScratch<Q, M> &ws, const uint8_t *Rs, int lane,
                                                    long long *tdeps, NextTask &nt) {
@@ -692,7 +691,7 @@ __device__ __forceinline__ long long run_far_strip(const FoldParams &P, const Se
         for (int p2 = 0; p2 < S / 2; ++p2)
 #pragma unroll
             for (int r = 0; r < T; ++r) m2[p2][r] = 0u;
-        far_strip_tv<Q, S>(P, sd, I, J0, Seff, Ka, Kb, m2, ws, Rs, lane);
+        far_strip_tv<Q, S, MEMO>(P, sd, I, J0, Seff, Ka, Kb, m2, ws, Rs, lane);
         if (P.trace) tdone = (long long)gtimer();
         nt.start(lane);
         if (lane < T) {
@@ -752,7 +751,7 @@ struct NearCol {
     bool failed;                  // the last tile stopped on a failed wait
 };
 
-template <int Q, int M, bool COL>
+template <int Q, int M, bool COL, bool MEMO>
 __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc &sd, int I, int J, int nfar,
                                               WarpScratch<Q, M> &ws, const uint8_t *Rs, int lane, long long *tdeps,
                                               NearCol<Q, M> &cs) {
@@ -885,8 +884,8 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int idx = e * 32 + lane;
-                memo_ensure<Q, M>(P, Rs, fv[e] & C::BMASK, idx < T * G, lane);
-                memo_ensure<Q, M>(P, Rs, fb[e] & C::BMASK, idx < T * G && lateB, lane);
+                memo_ensure<Q, M, MEMO>(Rs, fv[e] & C::BMASK, idx < T * G, lane);
+                memo_ensure<Q, M, MEMO>(Rs, fb[e] & C::BMASK, idx < T * G && lateB, lane);
                 if (idx < T * G) {
                     // the row's word for group gl: A, or -32768 while the group is not complete
                     // below the row (gl*q <= row), and the R-row offset of h
@@ -1047,7 +1046,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int idx = e * 32 + lane;
-            memo_ensure<Q, M>(P, Rs, fa[e] & C::BMASK, idx < T * G && lateA, lane);
+            memo_ensure<Q, M, MEMO>(Rs, fa[e] & C::BMASK, idx < T * G && lateA, lane);
             if (idx < T * G) ws.lrf[0][idx / G][idx % G] = group_word<Q>(fa[e]);
         }
     } else {
@@ -1432,25 +1431,22 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 }
 
 // ---------------------------------------------------------------- kernel
-template <int Q, int M>
+// MEMO: Section 3.2's partially memoised variant (R rows tabulated on first sight in each CTA)
+template <int Q, int M, bool MEMO>
 __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
     extern __shared__ __align__(16) uint8_t smem[];
     using C = Cfg<Q, M>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint8_t *Rs = smem;
-    if constexpr (memo_words<Q, M>() > 0) {
+    if constexpr (MEMO && memo_words<Q, M>() > 0) {
         // memoised R: no table yet, no row tabulated
-        if (P.memo) {
-            unsigned *bits = reinterpret_cast<unsigned *>(smem + memo_offset<Q, M>());
-            for (int v = threadIdx.x; v < memo_words<Q, M>(); v += blockDim.x) bits[v] = 0u;
-        }
-    }
-    if constexpr (C::RBYTES > 0) {
+        unsigned *bits = reinterpret_cast<unsigned *>(smem + memo_offset<Q, M>());
+        for (int v = threadIdx.x; v < memo_words<Q, M>(); v += blockDim.x) bits[v] = 0u;
+    } else if constexpr (C::RBYTES > 0) {
         const uint4 *src = reinterpret_cast<const uint4 *>(P.rtab);
         uint4 *dst = reinterpret_cast<uint4 *>(smem);
         // the device copy of R is padded to a multiple of 256 bytes, so rounding up stays in bounds
-        if (!P.memo)
-            for (int v = threadIdx.x; v < (C::RBYTES + 15) / 16; v += blockDim.x) dst[v] = __ldg(src + v);
+        for (int v = threadIdx.x; v < (C::RBYTES + 15) / 16; v += blockDim.x) dst[v] = __ldg(src + v);
     }
     WarpScratch<Q, M> *wsb = reinterpret_cast<WarpScratch<Q, M> *>(smem + round_up(C::RBYTES, 128));
     WarpScratch<Q, M> &ws = wsb[warp];
@@ -1480,7 +1476,7 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
             const int4 tk = P.tasks[idx];
             long long t0 = 0, tdeps[4] = {0, 0, 0, 0};
             if (P.trace && lane == 0) t0 = (long long)gtimer();
-            const long long tmid = run_near<Q, M, true>(P, sd, I, J, tk.z, ws, Rs, lane, tdeps, cs);
+            const long long tmid = run_near<Q, M, true, MEMO>(P, sd, I, J, tk.z, ws, Rs, lane, tdeps, cs);
             if (P.trace && lane == 0) {
                 long long *rec = P.trace + (size_t)idx * kTraceWords;
                 rec[0] = ((long long)(blockIdx.x * kWarpsPerCta + warp) << 32) | (unsigned)idx;
@@ -1524,10 +1520,10 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
             none.prod = nullptr;
             none.consumer = false;
             none.cnt_ok = false;
-            tmid = run_near<Q, M, false>(P, sd, I, J, tk.z, ws, Rs, lane, tdeps, none);
+            tmid = run_near<Q, M, false, MEMO>(P, sd, I, J, tk.z, ws, Rs, lane, tdeps, none);
         }
-        else if (ty == kTaskFar) tmid = run_far<Q, M>(P, sd, I, J, tk.z, tk.w, ws, Rs, lane, tdeps, nt);
-        else tmid = run_far_strip<Q, M>(P, sd, I, J, tk.z, tk.w, ws, Rs, lane, tdeps, nt);
+        else if (ty == kTaskFar) tmid = run_far<Q, M, MEMO>(P, sd, I, J, tk.z, tk.w, ws, Rs, lane, tdeps, nt);
+        else tmid = run_far_strip<Q, M, MEMO>(P, sd, I, J, tk.z, tk.w, ws, Rs, lane, tdeps, nt);
         if (P.trace && lane == 0) {
             long long *rec = P.trace + (size_t)idx * kTraceWords;
             rec[0] = ((long long)(blockIdx.x * kWarpsPerCta + warp) << 32) | (unsigned)idx;
@@ -1544,12 +1540,12 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
     }
 }
 
-template <int Q, int M>
+template <int Q, int M, bool MEMO = false>
 inline cudaError_t launch_q(const FoldParams &p, int grid, cudaStream_t st) {
     size_t sm = smem_bytes_for<Q, M>();
-    cudaError_t e = cudaFuncSetAttribute(fold_kernel<Q, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(fold_kernel<Q, M, MEMO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    fold_kernel<Q, M><<<grid, kThreads, sm, st>>>(p);
+    fold_kernel<Q, M, MEMO><<<grid, kThreads, sm, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -1557,9 +1553,9 @@ template <int Q, int M>
 inline int blocks_per_sm_q() {
     int nb = 0;
     size_t sm = smem_bytes_for<Q, M>();
-    if (cudaFuncSetAttribute(fold_kernel<Q, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    if (cudaFuncSetAttribute(fold_kernel<Q, M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fold_kernel<Q, M>, kThreads, sm) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fold_kernel<Q, M, false>, kThreads, sm) != cudaSuccess) return 0;
     return nb;
 }
 
