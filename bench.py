@@ -471,7 +471,7 @@ def main():
         pairs = int((part_s > torch.arange(n, device=dev)).sum().item())
         assert pairs == r_tv["max_pairs"]
         structure = {"ms_fold_and_traceback": min(ts), "ms_traceback": min(ts) - statistics.mean(r_tv["step_ms"]),
-                     "pairs": pairs, "note": "fold_structure_dev: the fold, then the one-block traceback kernel"}
+                     "pairs": pairs, "note": "fold_structure_dev: the fold, then the traceback (intervals traced in parallel by warps)"}
         del ws_s
 
     # ---- trace of one fold (optional)

@@ -732,9 +732,9 @@ int fold_rtable(fold_ctx *ctx, uint8_t *out, int64_t cap) {
     return status_from_cuda(e);
 }
 
-// Structure workspace: the fold's, then the traceback's stack of pending intervals.
+// Structure workspace: the fold's, then the traceback's queue of pending intervals.
 static size_t structure_bytes(size_t fold_bytes, int n) {
-    return align_up(fold_bytes, 256) + align_up(sizeof(int2) * (size_t)std::max(n, 1), 256);
+    return align_up(fold_bytes, 256) + align_up(traceback_scratch_bytes(n), 256);
 }
 
 int64_t fold_structure_workspace_bytes(fold_ctx *ctx, int32_t n) {
@@ -756,14 +756,15 @@ int fold_structure_dev(fold_ctx *ctx, const uint8_t *d_codes, int32_t n, void *d
     if (rc) return rc;
     if (n == 1) return status_from_cuda(cudaMemsetAsync(d_partner, 0xff, sizeof(int32_t), st));
     if (n >= 2) {
-        int2 *stack = reinterpret_cast<int2 *>(ws + align_up(fold_bytes, 256));
+        void *scratch = ws + align_up(fold_bytes, 256);
         const int16_t *drow;
         const uint8_t *codes;
         int stride;
         single_table(ctx, n, ws, &drow, &stride, &codes);
-        cudaError_t e = launch_traceback(drow, stride, codes, n, ctx->pair64, stack, d_partner, d_max_pairs, FOLD_ECUDA, st);
+        cudaError_t e = launch_traceback(drow, stride, codes, n, ctx->pair64, scratch, d_partner, d_max_pairs, FOLD_ECUDA,
+                                         ctx->timeout_ms * 1000000LL, ctx->sm_count, st);
         if (e != cudaSuccess) return status_from_cuda(e);
-        ctx->launches += 1;
+        ctx->launches += 3;   // init, parallel walk, check
     }
     return FOLD_OK;
 }

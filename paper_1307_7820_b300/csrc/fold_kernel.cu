@@ -5,9 +5,13 @@
 //                         (q-1)-bit difference vectors.
 //   extract / pad / finalize   data movement around the persistent kernel.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <type_traits>
 #include <stdint.h>
 
 #include "fold_common.h"
+#include "fold_kernel.cuh"
 #include "kernels.h"
 
 namespace fold {
@@ -126,93 +130,218 @@ int fold_blocks_per_sm(int q, int method) {
 // beside D; here the argmax is re-evaluated from D at each cell visited, in a fixed order of
 // preference: the split k = i+1 (base i unpaired) if D(i,j) = D(i+1,j); else the pair (i,j) if
 // b(S_i,S_j) = 1 and D(i,j) = D(i+1,j-1) + 1; else the smallest k in [i+2, j] with D(i,j) =
-// D(i,k-1) + D(k,j).  One block: thread 0 follows unpaired bases and pairs (each step reads two
-// cells), the whole block searches a split's k range, blockDim candidates at a time.  The pending
-// intervals live in `stack` (n entries).  partner[x] = the base paired with x, or -1.  *result is
-// the fold's answer D(0,n-1) (or -status if the fold failed, then nothing is traced); it becomes
-// -fail_code if the trace finds no argmax somewhere, runs past its step bound, or ends with a
-// different number of pairs (the table would not be one of Eq. 1).
-__global__ void traceback_kernel(const int16_t *Drow, int Np, const uint8_t *codes, int n, unsigned long long pair64,
-                                 int2 *stack, int32_t *partner, int32_t *result, int fail_code) {
-    __shared__ int s_i, s_j, s_dij, s_k, s_act;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int x = tid; x < n; x += nt) partner[x] = -1;
-    // the fold failed (its answer is -status): no table to trace
-    if (*(volatile const int32_t *)result < 0) return;
-    int status = 0, pairs = 0;   // thread 0's
-    auto DV = [&](int a, int b) -> int { return a >= b ? 0 : (int)Drow[(size_t)a * Np + b]; };
-    int top = 0, steps = 0;   // thread 0's stack depth and step count
-    int ci = 0, cj = n - 1;   // thread 0's current interval (empty when ci >= cj)
-    __syncthreads();
+// D(i,k-1) + D(k,j).  The two intervals a split leaves, [i, k-1] and [k, j], are traced
+// independently, so warps take intervals from a queue: a warp walks its interval and, at a split,
+// queues [k, j] and goes on with [i, k-1].  The result does not depend on which warp traces what.
+// Walking: an 8 x 16 window of the table (rows i+1.., columns ..j) and the bases of its rows and
+// columns are staged in shared memory by one round of loads and serve the unpaired and pair steps
+// inside it; a split's k range is searched 128 candidates per round (4 per lane, ballots in
+// increasing k).  Queue: slots claimed in order (head) and published with a release of
+// ready[slot]; one 64-bit word counts queued intervals (high half, which also numbers the slots)
+// and finished ones (low half): the trace is over when they are equal, so a warp waiting on a slot
+// that is never filled stops then.  Every wait is bounded.  partner[x] = the base paired with x, or
+// -1 (set by the caller).
+namespace {
+constexpr int kTbLine = 32;                  // ints per 128-byte line: each counter on its own line
+constexpr int kTbRows = 8, kTbCols = 16;     // window of the walk
+constexpr int kTbWarps = 4;                  // warps per block
+struct TbArgs {
+    const int16_t *Drow;
+    int Np, n;
+    const uint8_t *codes;
+    unsigned long long pair64;
+    int2 *queue;       // intervals (n + 2 slots)
+    int *qval;         // D of each queued interval
+    int *ready;        // slot published (zeroed by the caller)
+    int *state;        // head | queued-finished word | pairs | error, kTbLine ints apart
+    int32_t *partner;
+    const int32_t *result;
+    long long timeout_ns;
+};
+}
+
+__global__ void traceback_init_kernel(TbArgs A) {
+    // the fold failed (its answer is -status): nothing to trace
+    const int root = *(volatile const int32_t *)A.result;
+    A.state[0] = 0;
+    *reinterpret_cast<unsigned long long *>(A.state + kTbLine) = root >= 0 ? (1ull << 32) : 0ull;
+    A.state[2 * kTbLine] = 0;
+    A.state[3 * kTbLine] = 0;
+    if (root >= 0) {
+        A.queue[0] = make_int2(0, A.n - 1);
+        A.qval[0] = root;
+        A.ready[0] = 1;
+    }
+}
+
+static __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(32 * kTbWarps) traceback_par_kernel(TbArgs A) {
+    __shared__ int16_t s_win[kTbWarps][kTbRows][kTbCols];
+    __shared__ uint8_t s_br[kTbWarps][kTbRows], s_bc[kTbWarps][kTbCols];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    int *head = A.state, *err = A.state + 3 * kTbLine;
+    unsigned long long *qf = reinterpret_cast<unsigned long long *>(A.state + kTbLine);
+    const int cap = A.n + 2, n = A.n, Np = A.Np;
+    auto DV = [&](int a, int b) -> int { return a >= b ? 0 : (int)__ldcg(A.Drow + (size_t)a * Np + b); };
+    int pairs = 0;
     for (;;) {
-        if (tid == 0) {
-            int act = 0;   // 0: finished, 2: a split to search
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(head, 1);
+        idx = __shfl_sync(FULL, idx, 0);
+        if (idx >= cap) break;
+        int ok = 0;
+        if (lane == 0) {
+            const unsigned long long t0 = gtimer();
+            unsigned ns = 32;
+            for (unsigned it = 0;; ++it) {
+                if (ld_acquire(A.ready + idx)) { ok = 1; break; }
+                if ((it & 7u) == 7u) {   // the shared counters, seldom
+                    const unsigned long long v = ld_acquire64(qf);
+                    if ((unsigned)(v >> 32) == (unsigned)v || ld_relaxed(err) != 0) break;
+                    if ((long long)(gtimer() - t0) > A.timeout_ns) {
+                        atomicCAS(err, 0, 1);
+                        break;
+                    }
+                }
+                __nanosleep(ns);
+                ns = ns < 256 ? 2 * ns : 256;
+            }
+        }
+        if (!__shfl_sync(FULL, ok, 0)) break;
+        const int2 e = __ldcg(A.queue + idx);
+        int i = e.x, j = e.y, dij = __ldcg(A.qval + idx);
+        bool bad = false;
+        while (i < j && !bad) {
+            // window: rows i+1..i+8, columns j-15..j (4 cells per lane), and its bases
+            const int wi = i, wj = j;
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int cell = lane * 4 + u;
+                const int r = wi + 1 + cell / kTbCols, cc = wj - (kTbCols - 1) + cell % kTbCols;
+                s_win[wp][cell / kTbCols][cell % kTbCols] = (int16_t)((cc >= 0 && r < n) ? DV(r, cc) : 0);
+            }
+            if (lane < kTbRows) s_br[wp][lane] = wi + lane < n ? A.codes[wi + lane] : 0;
+            if (lane < kTbCols) s_bc[wp][lane] = wj - lane >= 0 ? A.codes[wj - lane] : 0;
+            __syncwarp();
+            bool split = false;
             for (;;) {
-                if (ci >= cj) {
-                    if (top == 0) break;
-                    const int2 e = stack[--top];
-                    ci = e.x;
-                    cj = e.y;
+                if (i >= j) break;
+                const int dr = i - wi, dc = j - (wj - (kTbCols - 1));   // row i+1 of the window, column j
+                if (dr > kTbRows - 1 || dc < 1) break;                   // left the window: load the next one
+                if (dij == (int)s_win[wp][dr][dc]) {                     // base i unpaired
+                    ++i;
                     continue;
                 }
-                if (++steps > 4 * n + 8) {
-                    status = 1;
-                    break;
-                }
-                const int dij = DV(ci, cj);
-                if (dij == DV(ci + 1, cj)) {   // base ci unpaired
-                    ++ci;
-                    continue;
-                }
-                if (((pair64 >> (8 * codes[ci] + codes[cj])) & 1ull) && dij == DV(ci + 1, cj - 1) + 1) {
-                    partner[ci] = cj;
-                    partner[cj] = ci;
+                const int bi = s_br[wp][dr], bj = s_bc[wp][wj - j];
+                if (((A.pair64 >> (8 * bi + bj)) & 1ull) && dij == (int)s_win[wp][dr][dc - 1] + 1) {
+                    if (lane == 0) {
+                        A.partner[i] = j;
+                        A.partner[j] = i;
+                    }
                     ++pairs;
-                    ++ci;
-                    --cj;
+                    ++i;
+                    --j;
+                    --dij;
                     continue;
                 }
-                s_i = ci;
-                s_j = cj;
-                s_dij = dij;
-                s_k = 0x7fffffff;
-                act = 2;
+                split = true;
                 break;
             }
-            s_act = act;
-        }
-        __syncthreads();
-        if (s_act == 0) break;
-        const int i = s_i, j = s_j, dij = s_dij;
-        for (int base = i + 2; base <= j; base += nt) {
-            const int k = base + tid;
-            if (k <= j && DV(i, k - 1) + DV(k, j) == dij) atomicMin(&s_k, k);
-            __syncthreads();
-            const bool found = s_k != 0x7fffffff;
-            __syncthreads();
-            if (found) break;
-        }
-        if (tid == 0) {
-            const int k = s_k;
-            if (k == 0x7fffffff || top >= n) {   // no argmax: stop
-                status = 2;
-                ci = cj = 0;
-                top = 0;
-            } else {
-                stack[top++] = make_int2(k, j);
-                ci = i;
-                cj = k - 1;
+            if (i >= j || !split) continue;
+            // the smallest split k in [i+2, j]: 128 candidates in the first round (most splits are
+            // near i), then 1024 a round, all of a round's loads in flight at once
+            int k = -1, dl = 0, dk = 0;
+            auto scan = [&](auto width_tag, int base) {
+                constexpr int U = decltype(width_tag)::value;
+                int a[U], b[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int kk = base + 32 * u + lane;
+                    a[u] = kk <= j ? DV(i, kk - 1) : 0;
+                    b[u] = kk <= j ? DV(kk, j) : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int kk = base + 32 * u + lane;
+                    const unsigned m = __ballot_sync(FULL, kk <= j && a[u] + b[u] == dij);
+                    if (m && k < 0) {
+                        const int src = __ffs(m) - 1;
+                        k = base + 32 * u + src;
+                        dl = __shfl_sync(FULL, a[u], src);
+                        dk = __shfl_sync(FULL, b[u], src);
+                    }
+                }
+            };
+            scan(std::integral_constant<int, 4>(), i + 2);
+            for (int base = i + 2 + 128; base <= j && k < 0; base += 1024) scan(std::integral_constant<int, 32>(), base);
+            if (k < 0) {   // no argmax: the table is not one of Eq. 1
+                bad = true;
+                if (lane == 0) atomicCAS(err, 0, 2);
+                break;
             }
+            if (lane == 0) {
+                const int slot = (int)(atomicAdd(qf, 1ull << 32) >> 32);
+                if (slot < cap) {
+                    A.queue[slot] = make_int2(k, j);
+                    A.qval[slot] = dk;
+                    st_release(A.ready + slot, 1);
+                } else {
+                    atomicCAS(err, 0, 3);
+                }
+            }
+            j = k - 1;
+            dij = dl;
         }
-        __syncthreads();
+        __syncwarp();
+        if (lane == 0) atomicAdd(qf, 1ull);   // this interval is finished
+        if (bad) break;
     }
-    // a structure with as many pairs as the answer, or the answer becomes -fail_code
-    if (tid == 0 && (status != 0 || pairs != *result)) *result = -fail_code;
+    if (lane == 0 && pairs) atomicAdd(A.state + 2 * kTbLine, pairs);
+}
+
+__global__ void traceback_check_kernel(TbArgs A, int fail_code) {
+    const int root = *A.result;
+    if (root < 0) return;
+    if (A.state[3 * kTbLine] != 0 || A.state[2 * kTbLine] != root) *const_cast<int32_t *>(A.result) = -fail_code;
+}
+
+size_t traceback_scratch_bytes(int n) {
+    const size_t cap = (size_t)std::max(n, 1) + 2;
+    return ((8 * cap + 255) / 256 + (4 * cap + 255) / 256 + (4 * cap + 255) / 256) * 256 + 4 * kTbLine * 4;
 }
 
 cudaError_t launch_traceback(const int16_t *drow, int Np, const uint8_t *codes, int n, unsigned long long pair64,
-                             int2 *stack, int32_t *partner, int32_t *result, int fail_code, cudaStream_t st) {
-    traceback_kernel<<<1, 256, 0, st>>>(drow, Np, codes, n, pair64, stack, partner, result, fail_code);
+                             void *scratch, int32_t *partner, int32_t *result, int fail_code, long long timeout_ns,
+                             int sm_count, cudaStream_t st) {
+    const size_t cap = (size_t)std::max(n, 1) + 2;
+    uint8_t *b = reinterpret_cast<uint8_t *>(scratch);
+    TbArgs A;
+    A.Drow = drow;
+    A.Np = Np;
+    A.n = n;
+    A.codes = codes;
+    A.pair64 = pair64;
+    A.queue = reinterpret_cast<int2 *>(b);
+    A.qval = reinterpret_cast<int *>(b + (8 * cap + 255) / 256 * 256);
+    A.ready = reinterpret_cast<int *>(b + ((8 * cap + 255) / 256 + (4 * cap + 255) / 256) * 256);
+    A.state = reinterpret_cast<int *>(b + ((8 * cap + 255) / 256 + 2 * ((4 * cap + 255) / 256)) * 256);
+    A.partner = partner;
+    A.result = result;
+    A.timeout_ns = timeout_ns;
+    cudaError_t e = cudaMemsetAsync(A.ready, 0, 4 * cap, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(partner, 0xff, 4 * (size_t)n, st);
+    if (e != cudaSuccess) return e;
+    traceback_init_kernel<<<1, 1, 0, st>>>(A);
+    // enough warps for the intervals open at once (a few hundred at most for long folds)
+    const int blocks = std::max(1, std::min(sm_count, (n + 255) / 256));
+    traceback_par_kernel<<<blocks, 32 * kTbWarps, 0, st>>>(A);
+    traceback_check_kernel<<<1, 1, 0, st>>>(A, fail_code);
     return cudaGetLastError();
 }
 

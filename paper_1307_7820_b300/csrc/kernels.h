@@ -13,9 +13,12 @@ cudaError_t launch_finalize(const int *error, const int *results, int count, int
 cudaError_t launch_fold(const FoldParams &p, int q, int method, int grid, cudaStream_t st);
 cudaError_t launch_rtable(int q, uint8_t *canon, uint8_t *packed, cudaStream_t st);
 cudaError_t launch_extract(const int16_t *drow, int Np, int n, int16_t *out, cudaStream_t st);
-// Section 2 traceback of a finished table (one block); stack: n int2, partner: n int32
+// Section 2 traceback of a finished table (intervals traced in parallel); scratch:
+// traceback_scratch_bytes(n) bytes, partner: n int32; *result becomes -fail_code on failure
+size_t traceback_scratch_bytes(int n);
 cudaError_t launch_traceback(const int16_t *drow, int Np, const uint8_t *codes, int n, unsigned long long pair64,
-                             int2 *stack, int32_t *partner, int32_t *result, int fail_code, cudaStream_t st);
+                             void *scratch, int32_t *partner, int32_t *result, int fail_code, long long timeout_ns,
+                             int sm_count, cudaStream_t st);
 cudaError_t launch_pad_codes(const uint8_t *in, int n, int Np, uint8_t *out, cudaStream_t st);
 
 }  // namespace fold
