@@ -95,9 +95,12 @@ void build_one(int NT, int kc, int S, bool geometric, SeqTemplate &tp) {
             // blocks next to its two ends
             const int J0s = J / S * S;
             if (S > 1 && J0s - 2 >= I + S + 1) {
-                split_range(I + 2, I + S, kc, geometric, parts, tail);
+                // every block of either end range is last read from a tile on diagonal t-2 or
+                // earlier and is needed by tile (I,J) alone: one chunk per range (fewer tasks, no
+                // later than the last of its blocks)
+                split_range(I + 2, I + S, kc, false, parts, tail);
                 for (const auto &ck : parts) add(kTaskFar, I, J, J, ck.first, ck.second);
-                split_range(J0s - 1, J - 2, kc, geometric, parts, tail);
+                split_range(J0s - 1, J - 2, kc, false, parts, tail);
                 for (const auto &ck : parts) add(kTaskFar, I, J, J, ck.first, ck.second);
             } else {
                 split_range(I + 2, J - 2, kc, geometric, parts, tail);
