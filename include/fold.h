@@ -178,7 +178,13 @@ int fold_score(fold_ctx *ctx, const char *seq, int32_t n, int32_t *max_pairs, in
  *   d_D_out    nullable device buffer of n*n int16 for the full table.
  * Inside the workspace D is kept twice as int16 (row-major and column-major,
  * padded to a multiple of the tile edge), plus the packed difference vectors
- * and the tile flags of the persistent kernel. */
+ * and the tile flags of the persistent kernel.
+ * CUDA graphs: fold_score_dev may be recorded by stream capture (e.g. into a
+ * torch.cuda.CUDAGraph) once one uncaptured call has folded that length with
+ * the same options (it builds the task list, which needs allocations); a
+ * replay then folds whatever the captured code buffers hold.  While a stream
+ * is capturing, a length without a task list, FOLD_OPT_TIMING and
+ * FOLD_OPT_TRACE return FOLD_EINVAL and nothing is recorded. */
 int64_t fold_workspace_bytes(fold_ctx *ctx, int32_t n);
 int fold_score_dev(fold_ctx *ctx, const uint8_t *d_codes, int32_t n, void *d_ws, int64_t ws_bytes,
                    int32_t *d_max_pairs, int16_t *d_D_out, void *stream);

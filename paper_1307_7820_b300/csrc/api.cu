@@ -291,7 +291,7 @@ bool encode_seq(const char *seq, int n, uint8_t *out) {
 
 // Cached device schedule + descriptor for a single sequence of length n.
 int single_schedule(fold_ctx *ctx, int n, const Plan &pl, const int4 **tasks, int *ntasks, int *nnear,
-                    bool *layout_ok, const SeqDesc **d_sd) {
+                    bool *layout_ok, const SeqDesc **d_sd, bool capturing) {
     int NT = pl.NTs[0];
     const FoldOpts o = single_opts(ctx, n);
     int kc = o.kc > 0 ? o.kc : kc_auto(NT);
@@ -302,6 +302,8 @@ int single_schedule(fold_ctx *ctx, int n, const Plan &pl, const int4 **tasks, in
     if (ctx->test_drop_task) key = -key - 1;   // separate cache entry for the fault-injection schedule
     auto it = ctx->sched_cache.find(key);
     if (it == ctx->sched_cache.end()) {
+        // building the list allocates and copies synchronously: not while a stream is being captured
+        if (capturing) return FOLD_EINVAL;
         std::vector<int4> tv;
         build_schedule(pl.NTs, kc, strip_of(ctx->q, ctx->method), tv);
         if (ctx->test_drop_task) {
@@ -470,20 +472,28 @@ static void single_table(const fold_ctx *ctx, int n, uint8_t *ws, const int16_t 
 
 int enqueue_single(fold_ctx *ctx, const uint8_t *d_codes, int n, uint8_t *ws, size_t ws_bytes, int32_t *d_out,
                    int16_t *d_D, cudaStream_t st) {
+    // stream capture (CUDA graphs): only stream work may be recorded, so no allocation, timing or trace
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return FOLD_ECUDA;
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
+    if (capturing && (ctx->timing || ctx->trace)) return FOLD_EINVAL;
     if (ctx->method == kSliding) return enqueue_sliding(ctx, d_codes, n, ws, ws_bytes, d_out, d_D, st);
     if (ctx->method == kFg) return enqueue_fg(ctx, d_codes, n, ws, ws_bytes, d_out, d_D, st);
     int32_t len = n;
     Plan pl = make_plan(&len, 1, ctx->q, ctx->method);
     if (ws_bytes < pl.bytes) return FOLD_ENOMEM;
+    // the task list first: a refusal leaves nothing enqueued (or recorded)
+    const int4 *tasks = nullptr;
+    int ntasks = 0, nnear = 0;
+    bool layout_ok = false;
+    const SeqDesc *d_sd = nullptr;
+    if (n >= 1) {
+        int rc = single_schedule(ctx, n, pl, &tasks, &ntasks, &nnear, &layout_ok, &d_sd, capturing);
+        if (rc) return rc;
+    }
     cudaError_t e = cudaMemsetAsync(ws, 0, pl.zero_bytes, st);
     if (e != cudaSuccess) return status_from_cuda(e);
     if (n >= 1) {
-        const int4 *tasks;
-        int ntasks, nnear;
-        bool layout_ok;
-        const SeqDesc *d_sd;
-        int rc = single_schedule(ctx, n, pl, &tasks, &ntasks, &nnear, &layout_ok, &d_sd);
-        if (rc) return rc;
         e = launch_pad_codes(d_codes, n, pl.sd[0].Np, ws + pl.off_codes, st);
         if (e != cudaSuccess) return status_from_cuda(e);
         FoldParams p = make_params(ctx, pl, ws, tasks, ntasks, d_sd);
