@@ -299,33 +299,23 @@ def main():
         return run_reference(a)
 
     import torch
-    from paper_1307_7820_b300 import fold, metrics, synth
+    from paper_1307_7820_b300 import fold, metrics, ranks, synth
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    rk = ranks.Ranks(backend="nccl", device=dev)
+    world, rank = rk.world, rk.rank
     torch.cuda.set_device(dev)
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
 
     def barrier_sync():
         torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
+        rk.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = rk.max
 
     n, q = a.n, a.q
     seq = synth.uniform(n, 1308)
@@ -481,16 +471,19 @@ def main():
         np.save(a.trace, fold.fold_trace_copy(tv.ctx))
         tv.option(fold.FOLD_OPT_TRACE, 0)
 
-    # ---- batched folding: 4096 sequences, log-uniform lengths in [64, 3000]
+    # ---- batched folding: 4096 sequences, log-uniform lengths in [64, 3000]; with several ranks
+    # each folds its longest-processing-time share (independent sequences, no collective)
     batch = None
     if not a.no_batch:
-        seqs = synth.batch(4096, 64, 3000, synth.SEED_BASE + 3)
+        all_seqs = synth.batch(4096, 64, 3000, synth.SEED_BASE + 3)
+        mine = ranks.partition_lpt([len(x) for x in all_seqs], world)[rank]
+        seqs = [all_seqs[k] for k in mine]
         tv.batch(seqs[:64])
         barrier_sync()
         t0 = time.perf_counter()
         res = tv.batch(seqs)
-        bt = time.perf_counter() - t0
-        bk = tv.option(fold.FOLD_OPT_KERNEL_NS) / 1e9
+        bt = max_over_ranks(time.perf_counter() - t0)
+        bk = max_over_ranks(tv.option(fold.FOLD_OPT_KERNEL_NS) / 1e9)
         # one-at-a-time baseline on a 1-in-16 sample, device-timed, scaled to all sequences
         sample = seqs[::16]
         loop_s = 0.0
@@ -507,9 +500,11 @@ def main():
             e1.synchronize()
             loop_s += e0.elapsed_time(e1) / 1e3
         loop_s *= len(seqs) / len(sample)
-        batch = {"sequences": len(seqs), "lengths": "log-uniform [64, 3000]", "seq_per_s_e2e": len(seqs) / bt,
-                 "seq_per_s_kernel": len(seqs) / bk if bk > 0 else None,
-                 "seq_per_s_one_at_a_time": len(seqs) / loop_s,
+        batch = {"sequences": len(all_seqs), "lengths": "log-uniform [64, 3000]",
+                 "ranks": world, "split": "longest processing time first across ranks" if world > 1 else None,
+                 "seq_per_s_e2e": len(all_seqs) / bt,
+                 "seq_per_s_kernel": len(all_seqs) / bk if bk > 0 else None,
+                 "seq_per_s_one_at_a_time": len(seqs) / loop_s,   # this rank's share on one GPU
                  "speedup_vs_one_at_a_time": (loop_s / bk) if bk > 0 else None,
                  "one_at_a_time_sample": "device time of every 16th sequence, scaled to 4096",
                  "total_cells": int(sum(metrics.cells(len(s)) for s in seqs)), "checksum": int(res.sum())}
@@ -595,8 +590,7 @@ def main():
         print(json.dumps(line), flush=True)
     tv.close()
     pl.close()
-    if dist is not None:
-        dist.destroy_process_group()
+    rk.close()
     return 0
 
 
