@@ -113,6 +113,8 @@ typedef struct fold_trace_rec {
     int32_t type;       /* 0 = tile (NEAR), 1 = middle-block chunk (FAR) */
     int32_t I, J;       /* tile coordinates */
     int32_t seq;        /* sequence index within the launch */
+    int32_t sm;         /* SM that ran the task (%smid) */
+    int32_t reserved;   /* 0 */
     int64_t t_start;    /* %globaltimer ns when the worker took the task */
     int64_t t_deps;     /* ns when the tiles it reads were published */
     int64_t t_mid;      /* tile: ns when the partial max over middle blocks was complete;

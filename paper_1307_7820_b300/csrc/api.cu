@@ -714,6 +714,8 @@ int64_t fold_trace_copy(fold_ctx *ctx, fold_trace_rec *out, int64_t cap) {
         o.t_aux[0] = r[7];
         o.t_aux[1] = r[8];
         o.t_aux[2] = r[9];
+        o.sm = (int32_t)r[10];
+        o.reserved = 0;
     }
     return count;
 }

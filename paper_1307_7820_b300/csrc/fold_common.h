@@ -17,7 +17,7 @@ constexpr int kColOff = 7;                      // Dcol offset: D(i,j) at Dcol[j
 constexpr int kRing = 8;                        // P (far partial max) ring depth in tile diagonals
 constexpr int kNeg16 = -32768;                  // int16 "minus infinity" for the row closure
 constexpr int kPadCode = 4;                     // padding base: pairs with nothing
-constexpr int kTraceWords = 10;                 // 64-bit words per task trace record
+constexpr int kTraceWords = 11;                 // 64-bit words per task trace record
 
 // kSliding: Section 4's organisation with per-cell vectors; kFg: Section 3.2's FG algorithm (each its
 // own per-column kernel, single folds only)

@@ -60,6 +60,11 @@ static __device__ __forceinline__ unsigned long long gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+static __device__ __forceinline__ unsigned smid() {
+    unsigned s;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(s));
+    return s;
+}
 
 // Lane 0 waits (bounded) until *p >= target; the verdict is broadcast.  On
 // timeout the error word is set; any error seen makes every worker stop.
@@ -1461,8 +1466,11 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
         // column mode: this warp computes the tiles of one column, bottom-up
         const SeqDesc sd = P.seqs[0];
         const int NT = sd.NT;
-        const int J = (int)blockIdx.x * P.cols_per_cta + warp;
-        if (warp >= P.cols_per_cta || J >= NT) return;
+        // the longest columns (the right end, whose chains set the fold's time) go to the CTAs
+        // launched first, away from the chunk CTAs that follow the tile CTAs in launch order
+        const int col_ctas = (NT + P.cols_per_cta - 1) / P.cols_per_cta;
+        const int J = (col_ctas - 1 - (int)blockIdx.x) * P.cols_per_cta + warp;
+        if ((int)blockIdx.x >= col_ctas || warp >= P.cols_per_cta || J >= NT) return;
         NearCol<Q, M> cs;
         cs.prod = warp > 0 ? &wsb[warp - 1] : nullptr;
         cs.consumer = (warp + 1 < P.cols_per_cta) && (J + 1 < NT);
@@ -1489,6 +1497,7 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
                 rec[7] = tdeps[1];
                 rec[8] = tdeps[2];
                 rec[9] = tdeps[3];
+                rec[10] = (long long)smid();
             }
             if (cs.failed) break;   // a wait gave up (its error is in P.error)
         }
@@ -1536,6 +1545,7 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
             rec[7] = tdeps[1];
             rec[8] = tdeps[2];
             rec[9] = tdeps[3];
+            rec[10] = (long long)smid();
         }
     }
 }

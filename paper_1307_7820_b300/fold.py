@@ -43,6 +43,7 @@ class TraceRec(ctypes.Structure):
     """struct fold_trace_rec"""
     _fields_ = [("worker", ctypes.c_int32), ("task", ctypes.c_int32), ("type", ctypes.c_int32),
                 ("I", ctypes.c_int32), ("J", ctypes.c_int32), ("seq", ctypes.c_int32),
+                ("sm", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("t_start", ctypes.c_int64), ("t_deps", ctypes.c_int64), ("t_mid", ctypes.c_int64),
                 ("t_end", ctypes.c_int64), ("t_aux", ctypes.c_int64 * 3)]
 
@@ -215,7 +216,7 @@ def fold_trace_copy(ctx: int, cap: int = 1 << 24) -> np.ndarray:
     if k < 0:
         raise FoldError(-k, "fold_trace_copy")
     dt = np.dtype([("worker", "i4"), ("task", "i4"), ("type", "i4"), ("I", "i4"), ("J", "i4"), ("seq", "i4"),
-                   ("t_start", "i8"), ("t_deps", "i8"), ("t_mid", "i8"), ("t_end", "i8"), ("t_aux", "i8", (3,))])
+                   ("sm", "i4"), ("reserved", "i4"), ("t_start", "i8"), ("t_deps", "i8"), ("t_mid", "i8"), ("t_end", "i8"), ("t_aux", "i8", (3,))])
     return np.frombuffer(bytes(buf)[: k * ctypes.sizeof(TraceRec)], dtype=dt).copy()
 
 
