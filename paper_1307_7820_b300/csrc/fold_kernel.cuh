@@ -801,7 +801,9 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     const int nn_next = (COL && I > 0) ? __ldg(&cs.tasks[(t + 1) * NT - (t + 1) * t / 2 + (I - 1)].z) : 0;
 
     // ---- inputs from tiles finished long before the neighbours, all loads in flight at once
-    unsigned Wp[16];           // packed W[c'][c] = D(JT+c'+1, j) for c' < c, sentinel otherwise
+    unsigned Wp[16];           // packed W[c'][c] = D(JT+c'+1, j) for c' < c, 0 for c' = c (the empty
+                               // interval: the closure then carries the column's own pair term),
+                               // sentinel otherwise
     uint32_t lcb[2][G];        // late-block column features (B << 16 | c) (two-vector)
     unsigned lcol[2][16];      // late-block columns as packed pairs (plain)
 #pragma unroll
@@ -858,7 +860,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll
             for (int mm = 0; mm < 16; ++mm) {
                 const int c0 = 2 * mm, c1 = 2 * mm + 1;
-                int w0 = kNeg16, w1 = kNeg16;
+                int w0 = (valid && c0 == c) ? 0 : kNeg16, w1 = (valid && c1 == c) ? 0 : kNeg16;
                 if (valid && c0 < c) w0 = ldcg16(Dcol + (size_t)j * PC + JT + c0 + 1 + kColOff);
                 if (valid && c1 < c) w1 = ldcg16(Dcol + (size_t)j * PC + JT + c1 + 1 + kColOff);
                 Wp[mm] = (unsigned)(w0 & 0xffff) | ((unsigned)w1 << 16);
@@ -1291,27 +1293,34 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
         }
     } else {
         int yold = old_terms(T - 1);
+        // closure over the row, D_c = max(Y_c, max_{c'<=c} Y'_c' + W[c'][c]).  Only the pair term of
+        // Y_c' can matter there: every other term of Y_c' is a split D(i,k-1) + D(k,JT+c'), and with
+        // W[c'][c] added it is at most D(i,k-1) + D(k,j) (superadditivity, Eq. 1), a term Y_c or the
+        // closure already holds.  So the exchanged value is Y'_c' = D(i+1, JT+c'-1) + b(S_i, S_{JT+c'})
+        // (W[c][c] = 0 brings in the column's own pair term); where b = 0 it is the split of
+        // D(i+1, j) = below into two disjoint parts, at most that and harmless.  Y' needs no select:
+        // lane c'-1 stores its own value of the row below plus column c''s pair bit at position c' of
+        // ws.y right after it computes it, and lane 31 stores the left column's value at position 0.
+        const unsigned pbn = __shfl_sync(FULL, pbits, (lane + 1) & 31);   // column c+1's pair bits
+        const int yslot = (c + 1) & 31;
+        {
+            const int bv = c == 31 ? (int)ws.left[T] : colT;
+            ws.y[(T - 1) & 1][yslot] = (int16_t)(bv + (int)((pbn >> (T - 1)) & 1u));
+        }
+        __syncwarp();
 #pragma unroll 1
         for (int r = T - 1; r >= 0; --r) {
-            const int pb = (int)((pbits >> r) & 1u);
-            // D(i+1, j-1): lane c-1's previous row; lane 0 reads the left column
-            const int blraw = __shfl_up_sync(FULL, below, 1);
-            const int bl = (c == 0) ? (int)ws.left[r + 1] : blraw;
-            // closure over the row, D_c = max(Y_c, max_{c'<c} Y_c' + W[c'][c]).  Only the pair term of
-            // Y_c' can matter there: every other term of Y_c' is a split D(i,k-1) + D(k,JT+c'), and with
-            // W[c'][c] added it is at most D(i,k-1) + D(k,j) (superadditivity, Eq. 1), a term Y_c or the
-            // closure already holds.  So the exchanged value is the pair term alone, a short chain.
-            const int v = (pb && valid) ? bl + 1 : kNeg16;
-            ws.y[r & 1][c] = (int16_t)v;
-            __syncwarp();
             // the closure's inputs go out first; the work below fills their latency
             const uint4 *yp = reinterpret_cast<const uint4 *>(ws.y[r & 1]);
             uint4 ya[4];
 #pragma unroll
             for (int v4 = 0; v4 < 4; ++v4) ya[v4] = yp[v4];
-            // the terms that do not go through the closure: pair, the split k = i+1 (D(i,i) +
-            // D(i+1,j)), and the old terms
-            int y = max(max(yold, pb + bl), below);
+            // the next row's pair bit (bit r-1 of pbn; 0 after the last row) and lane 31's left value
+            const int bn = (int)(((pbn << 1) >> r) & 1u);
+            const int ln = (int)ws.left[r] + bn;
+            // the terms that do not go through the closure: the split k = i+1 (D(i,i) + D(i+1,j))
+            // and the old terms
+            int y = max(yold, below);
             y = valid ? y : kNeg16;
             // old terms of the next row overlap with this closure (the last one is unused)
             yold = old_terms(max(r - 1, 0));
@@ -1327,6 +1336,10 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             const unsigned acc = __vmaxs2(__vmaxs2(a0, a1), __vmaxs2(a2, a3));
             int d = max(y, hmax2(acc));
             d = valid ? d : 0;
+            // the next row's exchanged value, ordered before the row's other stores (after the last
+            // row it lands in the buffer the next tile fills first)
+            ws.y[(r - 1) & 1][yslot] = (int16_t)(c == 31 ? ln : d + bn);
+            __syncwarp();
             publish(r, d, below);
             below = d;
             if constexpr (TV) {
@@ -1393,8 +1406,8 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll
             for (int mm = 0; mm < 16; ++mm) {
                 const int c0 = 2 * mm, c1 = 2 * mm + 1;
-                const int w0 = (valid && c0 < c) ? (int)tile[min(c0 + 1, T)][c] : kNeg16;
-                const int w1 = (valid && c1 < c) ? (int)tile[min(c1 + 1, T)][c] : kNeg16;
+                const int w0 = (valid && c0 < c) ? (int)tile[min(c0 + 1, T)][c] : (valid && c0 == c) ? 0 : kNeg16;
+                const int w1 = (valid && c1 < c) ? (int)tile[min(c1 + 1, T)][c] : (valid && c1 == c) ? 0 : kNeg16;
                 cs.Wp[mm] = (unsigned)(w0 & 0xffff) | ((unsigned)w1 << 16);
             }
         }
