@@ -9,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/fold.h"
@@ -276,17 +277,30 @@ cudaError_t launch_fold_instrumented(fold_ctx *ctx, FoldParams &p, cudaStream_t 
 }
 
 // Base letters to codes; returns false on an invalid letter.
-bool encode_seq(const char *seq, int n, uint8_t *out) {
-    for (int k = 0; k < n; ++k) {
-        switch (seq[k]) {
-            case 'A': case 'a': out[k] = 0; break;
-            case 'C': case 'c': out[k] = 1; break;
-            case 'G': case 'g': out[k] = 2; break;
-            case 'U': case 'u': out[k] = 3; break;
-            default: return false;
-        }
+namespace {
+// base -> code 0..3 (A, C, G, U in either case); every other byte -> 0x80
+struct CodeTable {
+    uint8_t v[256];
+    CodeTable() {
+        memset(v, 0x80, sizeof v);
+        v['A'] = v['a'] = 0;
+        v['C'] = v['c'] = 1;
+        v['G'] = v['g'] = 2;
+        v['U'] = v['u'] = 3;
     }
-    return true;
+};
+const CodeTable kCodes;
+}  // namespace
+
+bool encode_seq(const char *seq, int n, uint8_t *out) {
+    // a table lookup per base and one check at the end: no branch that depends on the base
+    unsigned bad = 0;
+    for (int k = 0; k < n; ++k) {
+        const uint8_t c = kCodes.v[(uint8_t)seq[k]];
+        bad |= c;
+        out[k] = c;
+    }
+    return (bad & 0x80u) == 0;
 }
 
 // Cached device schedule + descriptor for a single sequence of length n.
@@ -888,9 +902,32 @@ int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int3
     if (ensure_host(ctx->hstage, codes_bytes + sd_bytes + task_bytes + res_bytes)) return FOLD_ENOMEM;
     uint8_t *h = reinterpret_cast<uint8_t *>(ctx->hstage.ptr);
     uint8_t *hcodes = h;
-    memset(hcodes, kPadCode, codes_bytes);
-    for (int k = 0; k < count; ++k)
-        if (!encode_seq(seqs[k], lens[k], hcodes + pl.sd[k].code_off)) return FOLD_EINVAL;
+    {
+        // each sequence's codes, then its padding up to the next one's (a few threads for big batches)
+        std::vector<size_t> code_end((size_t)count);
+        for (int k = 0; k < count; ++k)
+            code_end[(size_t)k] = k + 1 < count ? (size_t)pl.sd[(size_t)k + 1].code_off : codes_bytes;
+        if (count > 0 && pl.sd[0].code_off > 0) memset(hcodes, kPadCode, (size_t)pl.sd[0].code_off);
+        std::vector<char> ok((size_t)count, 1);
+        auto enc = [&](int k0, int k1) {
+            for (int k = k0; k < k1; ++k) {
+                uint8_t *o = hcodes + pl.sd[(size_t)k].code_off;
+                ok[(size_t)k] = encode_seq(seqs[k], lens[k], o);
+                memset(o + lens[k], kPadCode, code_end[(size_t)k] - (size_t)pl.sd[(size_t)k].code_off - (size_t)lens[k]);
+            }
+        };
+        const size_t bases = codes_bytes;
+        const int nth = bases < (size_t(1) << 21) ? 1 : (int)std::min<unsigned>(8u, std::max(1u, std::thread::hardware_concurrency()));
+        if (nth == 1) {
+            enc(0, count);
+        } else {
+            std::vector<std::thread> th;
+            for (int w = 0; w < nth; ++w) th.emplace_back(enc, (int)((long long)count * w / nth), (int)((long long)count * (w + 1) / nth));
+            for (auto &x : th) x.join();
+        }
+        for (int k = 0; k < count; ++k)
+            if (!ok[(size_t)k]) return FOLD_EINVAL;
+    }
     memcpy(h + codes_bytes, pl.sd.data(), sizeof(SeqDesc) * count);
     build_schedule_into(pl.NTs, kc, strip, !flat, reinterpret_cast<int4 *>(h + codes_bytes + sd_bytes), ntasks);
     int32_t *hres = reinterpret_cast<int32_t *>(h + codes_bytes + sd_bytes + task_bytes);

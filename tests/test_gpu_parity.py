@@ -108,6 +108,25 @@ def test_batch_matches_single(folders):
             assert np.array_equal(D.astype(np.int32), ref)
 
 
+def test_batch_threaded_encode_case_and_invalid(folders):
+    # over 2 MB of bases: the host encodes the batch on several threads
+    f = folders(8)
+    seqs = synth.batch(900, 2000, 3000, 77)
+    mixed = [s.lower() if k % 3 == 0 else s for k, s in enumerate(seqs)]
+    r1 = f.batch(seqs)
+    assert np.array_equal(f.batch(mixed), r1)
+    k = int(np.argmin([len(s) for s in seqs]))
+    assert r1[k] == oracle.score(seqs[k])
+    for k in (1, 450, 899):
+        assert r1[k] == f.score(seqs[k])
+    bad = list(seqs)
+    bad[600] = bad[600][:10] + "T" + bad[600][11:]
+    with pytest.raises(fold.FoldError) as ei:
+        f.batch(bad)
+    assert ei.value.code == fold.FOLD_EINVAL
+    assert np.array_equal(f.batch(seqs), r1)   # the context is still usable
+
+
 def test_batch_many_short(folders):
     f = folders(8)
     seqs = synth.batch(300, 20, 300, 4242)
