@@ -99,11 +99,15 @@ enum fold_option {
     FOLD_OPT_BATCH_FLAT = 14, /* fold_batch's middle-block chunks: -1 = automatic / 1 = fixed size
                                  (FOLD_OPT_KCHUNK, default 64 blocks), 0 = the single fold's sizes
                                  (growing from both ends of each range) */
-    FOLD_OPT_R_MEMO = 15      /* Section 3.2's partially memoised variant (two-vector, q <= 9): 1 = each
+    FOLD_OPT_R_MEMO = 15,     /* Section 3.2's partially memoised variant (two-vector, q <= 9): 1 = each
                                  CTA starts with an empty R and tabulates the row R[h][*] against every
                                  column vector the first time one of its warps stages a horizontal
                                  vector h; 0 = the table precomputed at fold_init (default).  Results
                                  are identical; FOLD_EINVAL for q = 10, FOLD_EAGAIN while serving. */
+    FOLD_OPT_BATCH_GATHER = 16 /* fold_batch's task list: 1 = gathered on the device from device copies of
+                                 the per-size task templates, kept by the context (up to 1 GiB; only a
+                                 segment list is copied per call; default); 0 = built on the host and
+                                 copied whole.  Results are identical. */
 };
 
 /* One record per task of the last traced persistent launch. */

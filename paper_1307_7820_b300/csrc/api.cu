@@ -292,6 +292,62 @@ struct CodeTable {
 const CodeTable kCodes;
 }  // namespace
 
+// Device copies of task templates, at most kTemplateStoreTasks tasks (1 GiB).
+constexpr size_t kTemplateStoreTasks = size_t(64) << 20;
+
+// The first task (in ctx->tstore) of every template in tpls, uploading those not there yet; false
+// when they do not fit the store (the caller then builds the list on the host).
+bool dev_templates(fold_ctx *ctx, const std::vector<std::shared_ptr<const SeqTemplate>> &tpls,
+                   std::vector<size_t> &first, cudaStream_t st) {
+    size_t need_all = 0, need_new = 0;
+    for (const auto &t : tpls) {
+        need_all += t->tasks.size();
+        if (!ctx->tstore_at.count(t.get())) need_new += t->tasks.size();
+    }
+    if (need_all > kTemplateStoreTasks) return false;
+    if (need_new > 0) {
+        // nothing that reads the store may still run while it is rewritten or moved
+        if (cudaStreamSynchronize(st) != cudaSuccess) { cudaGetLastError(); return false; }
+        if (ctx->tstore_used + need_new > kTemplateStoreTasks) {
+            ctx->tstore_at.clear();   // start over with this batch's templates
+            ctx->tstore_used = 0;
+            need_new = need_all;
+        }
+        const size_t want = (ctx->tstore_used + need_new) * sizeof(int4);
+        if (want > ctx->tstore.bytes) {
+            const size_t grow = std::min(std::max(want, 2 * ctx->tstore.bytes), kTemplateStoreTasks * sizeof(int4));
+            void *p = nullptr;
+            if (cudaMalloc(&p, grow) != cudaSuccess) { cudaGetLastError(); return false; }
+            if (ctx->tstore_used &&
+                (cudaMemcpyAsync(p, ctx->tstore.ptr, ctx->tstore_used * sizeof(int4), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                 cudaStreamSynchronize(st) != cudaSuccess)) {
+                cudaFree(p);
+                cudaGetLastError();
+                return false;
+            }
+            if (ctx->tstore.ptr) cudaFree(ctx->tstore.ptr);
+            ctx->tstore.ptr = p;
+            ctx->tstore.bytes = grow;
+        }
+    }
+    first.resize(tpls.size());
+    for (size_t k = 0; k < tpls.size(); ++k) {
+        auto it = ctx->tstore_at.find(tpls[k].get());
+        if (it == ctx->tstore_at.end()) {
+            const size_t at = ctx->tstore_used, cnt = tpls[k]->tasks.size();
+            if (cnt && cudaMemcpy(static_cast<int4 *>(ctx->tstore.ptr) + at, tpls[k]->tasks.data(), cnt * sizeof(int4),
+                                  cudaMemcpyHostToDevice) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            ctx->tstore_used += cnt;
+            it = ctx->tstore_at.emplace(tpls[k].get(), std::make_pair(tpls[k], at)).first;
+        }
+        first[k] = it->second.second;
+    }
+    return true;
+}
+
 bool encode_seq(const char *seq, int n, uint8_t *out) {
     // a table lookup per base and one check at the end: no branch that depends on the base
     unsigned bad = 0;
@@ -610,6 +666,7 @@ void fold_destroy(fold_ctx *ctx) {
     if (ctx->dout.ptr) cudaFree(ctx->dout.ptr);
     if (ctx->hstage.ptr) cudaFreeHost(ctx->hstage.ptr);
     if (ctx->trace_buf.ptr) cudaFree(ctx->trace_buf.ptr);
+    if (ctx->tstore.ptr) cudaFree(ctx->tstore.ptr);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -662,6 +719,10 @@ int fold_set_option(fold_ctx *ctx, int option, int64_t value) {
             if (value < -1 || value > 1) return FOLD_EINVAL;
             ctx->batch_flat_opt = (int)value;
             return FOLD_OK;
+        case FOLD_OPT_BATCH_GATHER:
+            if (value < 0 || value > 1) return FOLD_EINVAL;
+            ctx->batch_gather = (int)value;
+            return FOLD_OK;
         case FOLD_OPT_R_MEMO:
             if (value < 0 || value > 1 || (value == 1 && ctx->q >= 10)) return FOLD_EINVAL;
             if (ctx->serve) return FOLD_EAGAIN;
@@ -688,6 +749,7 @@ int fold_get_option(fold_ctx *ctx, int option, int64_t *value) {
         case FOLD_OPT_COLUMNS: *value = ctx->columns_opt; return FOLD_OK;
         case FOLD_OPT_BATCH_FLAT: *value = ctx->batch_flat_opt; return FOLD_OK;
         case FOLD_OPT_R_MEMO: *value = ctx->r_memo; return FOLD_OK;
+        case FOLD_OPT_BATCH_GATHER: *value = ctx->batch_gather; return FOLD_OK;
         case FOLD_OPT_KERNEL_NS: {
             if (!ctx->ev_pending) { *value = 0; return FOLD_OK; }
             float ms = 0.f;
@@ -893,13 +955,23 @@ int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int3
     const bool flat = ctx->batch_flat_opt != 0;
     int kc = ctx->kc_override > 0 ? ctx->kc_override : (flat ? 64 : kc_auto(maxNT));
     const int strip = strip_of(ctx->q, ctx->method);
-    const size_t ntasks = build_schedule_into(pl.NTs, kc, strip, !flat, nullptr, 0);
-    // host staging: codes (padded) | SeqDesc | tasks | results; the task list is written in place
+    std::vector<std::shared_ptr<const SeqTemplate>> tpls;
+    std::vector<ScheduleSeg> segs;
+    const size_t ntasks = schedule_segments(pl.NTs, kc, strip, !flat, tpls, segs);
+    if (ntasks > (size_t)INT32_MAX) return FOLD_EINVAL;
+    cudaStream_t st = ctx->stream;
+    // the task list is gathered on the device from device copies of the per-size templates (only
+    // the segment list crosses the bus) when they fit the store; else it is built here
+    std::vector<size_t> tfirst;
+    const bool gather = ntasks > 0 && ctx->batch_gather && dev_templates(ctx, tpls, tfirst, st);
+    // host staging: codes (padded) | SeqDesc | segments or tasks | results
     size_t codes_bytes = pl.off_drow - pl.off_codes;
     size_t sd_bytes = align_up(sizeof(SeqDesc) * count, 256);
     size_t task_bytes = align_up(ntasks * sizeof(int4), 256);
     size_t res_bytes = align_up(4 * (size_t)count, 256);
-    if (ensure_host(ctx->hstage, codes_bytes + sd_bytes + task_bytes + res_bytes)) return FOLD_ENOMEM;
+    const size_t seg_bytes = gather ? align_up(segs.size() * sizeof(int4), 256) : 0;
+    const size_t list_bytes = gather ? seg_bytes : task_bytes;
+    if (ensure_host(ctx->hstage, codes_bytes + sd_bytes + list_bytes + res_bytes)) return FOLD_ENOMEM;
     uint8_t *h = reinterpret_cast<uint8_t *>(ctx->hstage.ptr);
     uint8_t *hcodes = h;
     {
@@ -929,18 +1001,36 @@ int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int3
             if (!ok[(size_t)k]) return FOLD_EINVAL;
     }
     memcpy(h + codes_bytes, pl.sd.data(), sizeof(SeqDesc) * count);
-    build_schedule_into(pl.NTs, kc, strip, !flat, reinterpret_cast<int4 *>(h + codes_bytes + sd_bytes), ntasks);
-    int32_t *hres = reinterpret_cast<int32_t *>(h + codes_bytes + sd_bytes + task_bytes);
-    if (ensure_buf(ctx->ws, pl.bytes) || ensure_buf(ctx->aux, sd_bytes + task_bytes + res_bytes)) return FOLD_ENOMEM;
+    int4 *hlist = reinterpret_cast<int4 *>(h + codes_bytes + sd_bytes);
+    if (gather) {
+        for (size_t k = 0; k < segs.size(); ++k) {
+            const ScheduleSeg &sg = segs[k];
+            hlist[k] = make_int4((int)(tfirst[(size_t)sg.tpl] + (size_t)sg.first), sg.count, sg.seq, (int)sg.dst);
+        }
+    } else {
+        build_schedule_into(pl.NTs, kc, strip, !flat, hlist, ntasks);
+    }
+    int32_t *hres = reinterpret_cast<int32_t *>(h + codes_bytes + sd_bytes + list_bytes);
+    if (ensure_buf(ctx->ws, pl.bytes) || ensure_buf(ctx->aux, sd_bytes + task_bytes + res_bytes + seg_bytes))
+        return FOLD_ENOMEM;
     uint8_t *ws = reinterpret_cast<uint8_t *>(ctx->ws.ptr);
     uint8_t *aux = reinterpret_cast<uint8_t *>(ctx->aux.ptr);
     SeqDesc *d_sd = reinterpret_cast<SeqDesc *>(aux);
     int4 *d_tasks = reinterpret_cast<int4 *>(aux + sd_bytes);
     int32_t *d_res = reinterpret_cast<int32_t *>(aux + sd_bytes + task_bytes);
-    cudaStream_t st = ctx->stream;
+    int4 *d_segs = reinterpret_cast<int4 *>(aux + sd_bytes + task_bytes + res_bytes);
     cudaError_t e = cudaMemsetAsync(ws, 0, pl.zero_bytes, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ws + pl.off_codes, hcodes, codes_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(aux, h + codes_bytes, sd_bytes + task_bytes, cudaMemcpyHostToDevice, st);
+    if (gather) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(aux, h + codes_bytes, sd_bytes, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_segs, hlist, segs.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = launch_gather_tasks(static_cast<const int4 *>(ctx->tstore.ptr), d_segs, (int)segs.size(), d_tasks,
+                                    ctx->sm_count, st);
+        if (e == cudaSuccess) ctx->launches += 1;
+    } else if (e == cudaSuccess) {
+        e = cudaMemcpyAsync(aux, h + codes_bytes, sd_bytes + task_bytes, cudaMemcpyHostToDevice, st);
+    }
     if (e != cudaSuccess) return status_from_cuda(e);
     FoldParams p = make_params(ctx, pl, ws, d_tasks, (int)ntasks, d_sd);
     if (ntasks > 0) {

@@ -5,9 +5,11 @@
 #include <stdint.h>
 
 #include <map>
+#include <memory>
 #include <vector>
 
 #include "fold_common.h"
+#include "schedule.h"
 
 namespace fold {
 
@@ -65,8 +67,9 @@ struct fold_ctx {
     int test_drop_task = 0;
     int near_ctas_opt = -1;    // -1 automatic, 0 one shared queue, k > 0 k tile-only CTAs
     int columns_opt = -1;      // -1 automatic, 0 off, v >= 1 column mode with v columns per tile CTA
-    int batch_flat_opt = -1;
-    int r_memo = 0;            // FOLD_OPT_R_MEMO: tabulate R rows on first sight (two-vector, q <= 9)   // fold_batch chunks: -1 / 1 kc blocks each, 0 geometric sizes
+    int batch_flat_opt = -1;   // fold_batch chunks: -1 / 1 kc blocks each, 0 geometric sizes
+    int batch_gather = 1;      // FOLD_OPT_BATCH_GATHER: fold_batch's list gathered on the device
+    int r_memo = 0;            // FOLD_OPT_R_MEMO: tabulate R rows on first sight (two-vector, q <= 9)
     // tuned single-fold settings per size bucket (fold_tune / fold_tune_load); used when no option
     // forces a layout or a chunk size
     std::map<int, fold::TuneEntry> tune;
@@ -77,6 +80,11 @@ struct fold_ctx {
     std::map<long long, fold::CachedSched> sched_cache;
     fold::DevBuf ws, aux, dout;
     fold::HostBuf hstage;
+    // device copies of the task templates fold_batch gathers its list from: the templates (held, so
+    // each stays the same object) and the index of their first task in tstore
+    fold::DevBuf tstore;
+    size_t tstore_used = 0;
+    std::map<const fold::SeqTemplate *, std::pair<std::shared_ptr<const fold::SeqTemplate>, size_t>> tstore_at;
     unsigned long long launches = 0;
     // kernel timing (FOLD_OPT_TIMING) and task tracing (FOLD_OPT_TRACE)
     int timing = 0;

@@ -406,6 +406,31 @@ cudaError_t launch_extract(const int16_t *drow, int Np, int n, int16_t *out, cud
     return cudaGetLastError();
 }
 
+// A batch's task list from device copies of the per-size templates: segment s = {first task in the
+// store, count, sequence index, position in the list}; a warp copies one segment, rewriting the
+// sequence index of every task.
+__global__ void gather_tasks_kernel(const int4 *__restrict__ store, const int4 *__restrict__ segs, int nseg,
+                                    int4 *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < nseg; s += warps) {
+        const int4 sg = __ldg(segs + s);
+        for (int e = lane; e < sg.y; e += 32) {
+            int4 v = __ldg(store + (size_t)sg.x + e);
+            v.x = sg.z;
+            out[(size_t)sg.w + e] = v;
+        }
+    }
+}
+
+cudaError_t launch_gather_tasks(const int4 *store, const int4 *segs, int nseg, int4 *out, int sm_count,
+                                cudaStream_t st) {
+    if (nseg <= 0) return cudaSuccess;
+    const int blocks = std::max(1, std::min((nseg + 7) / 8, 8 * std::max(sm_count, 1)));
+    gather_tasks_kernel<<<blocks, 256, 0, st>>>(store, segs, nseg, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pad_codes(const uint8_t *in, int n, int Np, uint8_t *out, cudaStream_t st) {
     int blocks = (Np + 255) / 256;
     if (blocks > 1024) blocks = 1024;

@@ -20,5 +20,9 @@ cudaError_t launch_traceback(const int16_t *drow, int Np, const uint8_t *codes, 
                              void *scratch, int32_t *partner, int32_t *result, int fail_code, long long timeout_ns,
                              int sm_count, cudaStream_t st);
 cudaError_t launch_pad_codes(const uint8_t *in, int n, int Np, uint8_t *out, cudaStream_t st);
+// out[segs[s].w + e] = store[segs[s].x + e] with .x = segs[s].z, for e < segs[s].y (a batch's task
+// list gathered from device copies of its templates)
+cudaError_t launch_gather_tasks(const int4 *store, const int4 *segs, int nseg, int4 *out, int sm_count,
+                                cudaStream_t st);
 
 }  // namespace fold

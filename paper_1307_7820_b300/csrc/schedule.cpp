@@ -188,59 +188,77 @@ void build_schedule(const std::vector<int> &NTs, int kc, int strip, std::vector<
     build_schedule_into(NTs, kc, strip, geometric, out.data(), out.size());
 }
 
-size_t build_schedule_into(const std::vector<int> &NTs, int kc, int strip, bool geometric, int4 *out, size_t cap) {
+size_t schedule_segments(const std::vector<int> &NTs, int kc, int strip, bool geometric,
+                         std::vector<std::shared_ptr<const SeqTemplate>> &tpls, std::vector<ScheduleSeg> &segs) {
     const int nseq = (int)NTs.size();
     int maxNT = 0;
     for (int v : NTs) maxNT = std::max(maxNT, v);
-    // one template per distinct size (a batch has few), then every sequence's copy interleaved:
-    // for each step t, the NEAR tasks of all sequences, then their chunks
-    std::map<int, std::shared_ptr<const SeqTemplate>> tpl;
-    for (int v : NTs)
-        if (v > 0 && !tpl.count(v)) tpl[v] = seq_template(v, kc, strip, geometric);
-    std::vector<const SeqTemplate *> tp((size_t)nseq, nullptr);
-    for (int q = 0; q < nseq; ++q)
-        if (NTs[q] > 0) tp[(size_t)q] = tpl[NTs[q]].get();
-    size_t total = 0;
-    for (int q = 0; q < nseq; ++q)
-        if (tp[(size_t)q]) total += tp[(size_t)q]->tasks.size();
-    if (!out || cap < total) return total;
-    // segments of the output in order (one sequence's NEAR tasks or chunks of one step), then
-    // copied by a few threads when the list is long
-    struct Seg {
-        const int4 *src;
-        int count, seq;
-        size_t dst;
-    };
-    std::vector<Seg> segs;
+    // one template per distinct size (a batch has few)
+    tpls.clear();
+    segs.clear();
+    std::map<int, int> index;
+    std::vector<int> tix((size_t)nseq, -1);
+    for (int q = 0; q < nseq; ++q) {
+        const int v = NTs[q];
+        if (v <= 0) continue;
+        auto it = index.find(v);
+        if (it == index.end()) {
+            it = index.emplace(v, (int)tpls.size()).first;
+            tpls.push_back(seq_template(v, kc, strip, geometric));
+        }
+        tix[(size_t)q] = it->second;
+    }
     size_t k = 0;
     for (int t = 0; t < maxNT; ++t) {
         for (int part = 0; part < 2; ++part) {
             for (int q = 0; q < nseq; ++q) {
-                const SeqTemplate *p = tp[(size_t)q];
-                if (!p || t >= NTs[q]) continue;
+                if (tix[(size_t)q] < 0 || t >= NTs[q]) continue;
+                const SeqTemplate *p = tpls[(size_t)tix[(size_t)q]].get();
                 const int a = part == 0 ? p->near_begin[t] : p->chunk_begin[t];
                 const int b = part == 0 ? p->chunk_begin[t] : p->near_begin[t + 1];
-                if (b > a) segs.push_back({p->tasks.data() + a, b - a, q, k});
+                if (b > a) segs.push_back({tix[(size_t)q], a, b - a, q, k});
                 k += (size_t)(b - a);
             }
         }
     }
+    return k;
+}
+
+size_t build_schedule_into(const std::vector<int> &NTs, int kc, int strip, bool geometric, int4 *out, size_t cap) {
+    if (!out) {
+        // the count alone: one template lookup per distinct size
+        std::map<int, size_t> size_of;
+        size_t total = 0;
+        for (int v : NTs) {
+            if (v <= 0) continue;
+            auto it = size_of.find(v);
+            if (it == size_of.end()) it = size_of.emplace(v, seq_template(v, kc, strip, geometric)->tasks.size()).first;
+            total += it->second;
+        }
+        return total;
+    }
+    std::vector<std::shared_ptr<const SeqTemplate>> tpls;
+    std::vector<ScheduleSeg> segs;
+    const size_t total = schedule_segments(NTs, kc, strip, geometric, tpls, segs);
+    if (cap < total) return total;
     auto copy = [&](size_t s0, size_t s1) {
         for (size_t g = s0; g < s1; ++g) {
-            const Seg &sg = segs[g];
+            const ScheduleSeg &sg = segs[g];
+            const int4 *src = tpls[(size_t)sg.tpl]->tasks.data() + sg.first;
             for (int e = 0; e < sg.count; ++e) {
-                int4 v = sg.src[e];
+                int4 v = src[e];
                 v.x = sg.seq;
                 out[sg.dst + (size_t)e] = v;
             }
         }
     };
+    // copied by a few threads when the list is long: the segments split into ranges of about
+    // equal task counts
     const unsigned hw = std::thread::hardware_concurrency();
     const int nth = total < (1u << 20) ? 1 : (int)std::max(1u, std::min(hw, 16u));
     if (nth == 1) {
         copy(0, segs.size());
     } else {
-        // split the segments into nth ranges of about equal task counts
         std::vector<std::thread> th;
         size_t g = 0;
         for (int w = 0; w < nth && g < segs.size(); ++w) {

@@ -26,6 +26,17 @@ struct SeqTemplate {
 // Built once per (NT, kc, strip, geometric) and shared (process-wide, thread-safe cache).
 std::shared_ptr<const SeqTemplate> seq_template(int NT, int kc, int strip, bool geometric);
 
+// A batch's list as segments, in the order build_schedule_into writes it (for each step t, the
+// NEAR tasks of tile diagonal t of every sequence, then every sequence's chunks placed at t):
+// segment k is tasks [first, first + count) of template tpls[tpl], written with sequence index seq
+// at position dst.  Returns the total number of tasks; tpls holds one template per distinct size.
+struct ScheduleSeg {
+    int tpl, first, count, seq;
+    size_t dst;
+};
+size_t schedule_segments(const std::vector<int> &NTs, int kc, int strip, bool geometric,
+                         std::vector<std::shared_ptr<const SeqTemplate>> &tpls, std::vector<ScheduleSeg> &segs);
+
 // Checks a single-sequence list (coverage, chunk counts, dependency order); 0 = valid.
 int check_schedule(int NT, int kc, int strip, const std::vector<int4> &tasks);
 

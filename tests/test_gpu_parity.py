@@ -127,6 +127,25 @@ def test_batch_threaded_encode_case_and_invalid(folders):
     assert np.array_equal(f.batch(seqs), r1)   # the context is still usable
 
 
+def test_batch_gather_and_host_lists_agree(folders):
+    # the task list gathered on the device from the context's template copies (default) and the one
+    # built on the host; new length mixes each call, so the device store grows and is reused
+    f = folders(8)
+    try:
+        for seed in (1, 2, 3):
+            seqs = synth.batch(300, 20 + 100 * seed, 800 * seed, 900 + seed)
+            f.option(fold.FOLD_OPT_BATCH_GATHER, 1)
+            a = f.batch(seqs)
+            f.option(fold.FOLD_OPT_BATCH_GATHER, 0)
+            b = f.batch(seqs)
+            assert np.array_equal(a, b)
+            for k in np.argsort([len(x) for x in seqs])[:3]:
+                assert a[k] == oracle.score(seqs[k])
+    finally:
+        f.option(fold.FOLD_OPT_BATCH_GATHER, 1)
+    assert f.option(fold.FOLD_OPT_BATCH_GATHER) == 1
+
+
 def test_batch_many_short(folders):
     f = folders(8)
     seqs = synth.batch(300, 20, 300, 4242)
