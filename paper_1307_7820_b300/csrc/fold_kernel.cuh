@@ -842,12 +842,28 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             }
         }
     }
+    // the flags a tile reads (not column mode): 0-3 old tiles (I,I), (J,J), (J-1,J) and (I,I+1) for
+    // the late blocks, 4-5 the neighbours (I,J-1) and (I+1,J); null = not read
+    auto flag_ptr = [&](int k) -> const int * {
+        return k == 0 ? flags + I * NT + I
+             : k == 1 ? flags + J * NT + J
+             : k == 2 ? (lateA ? flags + (J - 1) * NT + J : nullptr)
+             : k == 3 ? (lateB ? flags + I * NT + (I + 1) : nullptr)
+             : k == 4 ? flags + I * NT + (J - 1)
+             : k == 5 ? flags + (I + 1) * NT + J : nullptr;
+    };
+    unsigned nb_miss = 0;      // neighbour flags not seen set yet (bits 4 and 5)
     if (t >= 1) {
         if constexpr (!COL) {
-            if (!warp_wait_geq(flags + I * NT + I, 1, P, lane)) return 0;
-            if (!warp_wait_geq(flags + J * NT + J, 1, P, lane)) return 0;
-            if (lateA && !warp_wait_geq(flags + (J - 1) * NT + J, 1, P, lane)) return 0;
-            if (lateB && !warp_wait_geq(flags + I * NT + (I + 1), 1, P, lane)) return 0;
+            // lanes 0-5 acquire one flag each, so the usual case (all set) costs one round trip; the
+            // warp barrier orders every lane's later loads after the acquires (as in wait_geq_impl).
+            // An old tile not yet done is awaited now, a neighbour after the old tiles' loads.
+            const int *mine = flag_ptr(lane);
+            const unsigned miss = __ballot_sync(FULL, mine != nullptr && ld_acquire(mine) < 1);
+            __syncwarp();
+            for (unsigned m = miss & 0xfu; m; m &= m - 1)
+                if (!warp_wait_geq(flag_ptr(__ffs(m) - 1), 1, P, lane)) return 0;
+            nb_miss = miss & 0x30u;
         }
         int16_t dv[T];
 #pragma unroll
@@ -934,10 +950,8 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 
     // ---- the two neighbours that finish last
     if constexpr (!COL) {
-        if (t >= 1) {
-            if (!warp_wait_geq(flags + I * NT + (J - 1), 1, P, lane)) return 0;
-            if (!warp_wait_geq(flags + (I + 1) * NT + J, 1, P, lane)) return 0;
-        }
+        for (unsigned m = nb_miss; m; m &= m - 1)
+            if (!warp_wait_geq(flag_ptr(__ffs(m) - 1), 1, P, lane)) return 0;
     } else {
         if (t >= 1 && early) {
             const bool ok = prod ? wait_smem_geq(&prod->produced, cs.k, P.error, P.timeout_ns, lane)
