@@ -877,8 +877,15 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             for (int mm = 0; mm < 16; ++mm) {
                 const int c0 = 2 * mm, c1 = 2 * mm + 1;
                 int w0 = (valid && c0 == c) ? 0 : kNeg16, w1 = (valid && c1 == c) ? 0 : kNeg16;
-                if (valid && c0 < c) w0 = ldcg16(Dcol + (size_t)j * PC + JT + c0 + 1 + kColOff);
-                if (valid && c1 < c) w1 = ldcg16(Dcol + (size_t)j * PC + JT + c1 + 1 + kColOff);
+                // D(JT+c'+1, j): two-vector from the row-major table (one 64-byte row segment per
+                // load: batch kernel -6%); the plain kernel measured faster with its column copy
+                if constexpr (TV) {
+                    if (valid && c0 < c) w0 = ldcg16(Drow + (size_t)(JT + c0 + 1) * Np + j);
+                    if (valid && c1 < c) w1 = ldcg16(Drow + (size_t)(JT + c1 + 1) * Np + j);
+                } else {
+                    if (valid && c0 < c) w0 = ldcg16(Dcol + (size_t)j * PC + JT + c0 + 1 + kColOff);
+                    if (valid && c1 < c) w1 = ldcg16(Dcol + (size_t)j * PC + JT + c1 + 1 + kColOff);
+                }
                 Wp[mm] = (unsigned)(w0 & 0xffff) | ((unsigned)w1 << 16);
             }
         }
