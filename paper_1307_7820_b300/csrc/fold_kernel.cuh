@@ -97,6 +97,19 @@ static __device__ __noinline__ bool wait_geq_impl(const int *p, int target, int 
 static __device__ __forceinline__ bool warp_wait_geq(const int *p, int target, const FoldParams &P, int lane) {
     return wait_geq_impl(p, target, P.error, P.timeout_ns, lane);
 }
+// Up to three tile flags (null = none) acquired by lanes 0-2 at once, so the usual case (all set)
+// costs one round trip; the warp barrier orders every lane's later loads after the acquires (as in
+// wait_geq_impl).  A flag not yet set is then awaited by warp_wait_geq.
+static __device__ __forceinline__ bool warp_wait_flags(const int *f0, const int *f1, const int *f2, const FoldParams &P,
+                                                       int lane) {
+    const int *mine = lane == 0 ? f0 : lane == 1 ? f1 : lane == 2 ? f2 : nullptr;
+    const unsigned miss = __ballot_sync(FULL, mine != nullptr && ld_acquire(mine) < 1);
+    __syncwarp();
+    if ((miss & 1u) && !warp_wait_geq(f0, 1, P, lane)) return false;
+    if ((miss & 2u) && !warp_wait_geq(f1, 1, P, lane)) return false;
+    if ((miss & 4u) && !warp_wait_geq(f2, 1, P, lane)) return false;
+    return true;
+}
 
 // shared-memory flags between the warps of one CTA (column mode)
 static __device__ __forceinline__ int ld_acquire_cta(const int *p) {
@@ -505,9 +518,10 @@ __device__ __forceinline__ long long run_far(const FoldParams &P, const SeqDesc 
         if (lane == 0) atomicCAS(P.error, 0, kErrBadTask);
         return 0;
     }
-    if (!warp_wait_geq(flags + I * NT + Kb, 1, P, lane)) return 0;
-    if (!warp_wait_geq(flags + Ka * NT + J, 1, P, lane)) return 0;
-    if (J - I >= kRing && !warp_wait_geq(flags + I * NT + (J - kRing), 1, P, lane)) return 0;
+    // row strip (I, Kb), column strip (Ka, J) and, past the P ring's depth, the tile whose slot this reuses
+    if (!warp_wait_flags(flags + I * NT + Kb, flags + Ka * NT + J, J - I >= kRing ? flags + I * NT + (J - kRing) : nullptr,
+                         P, lane))
+        return 0;
     if (P.trace) tdeps[0] = (long long)gtimer();
     int m[T];
     if constexpr (M == kTwoVector) {
@@ -685,9 +699,9 @@ __device__ __forceinline__ long long run_far_strip(const FoldParams &P, const Se
         if (lane == 0) atomicCAS(P.error, 0, kErrBadTask);
         return 0;
     }
-    if (!warp_wait_geq(flags + I * NT + Kb, 1, P, lane)) return 0;
-    if (!warp_wait_geq(flags + Ka * NT + Jl, 1, P, lane)) return 0;
-    if (Jl - I >= kRing && !warp_wait_geq(flags + I * NT + (Jl - kRing), 1, P, lane)) return 0;
+    if (!warp_wait_flags(flags + I * NT + Kb, flags + Ka * NT + Jl,
+                         Jl - I >= kRing ? flags + I * NT + (Jl - kRing) : nullptr, P, lane))
+        return 0;
     if (P.trace) tdeps[0] = (long long)gtimer();
     long long tdone = 0;
     if constexpr (M == kTwoVector) {
