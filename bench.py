@@ -478,12 +478,18 @@ def main():
         all_seqs = synth.batch(4096, 64, 3000, synth.SEED_BASE + 3)
         mine = ranks.partition_lpt([len(x) for x in all_seqs], world)[rank]
         seqs = [all_seqs[k] for k in mine]
-        tv.batch(seqs[:64])
-        barrier_sync()
-        t0 = time.perf_counter()
-        res = tv.batch(seqs)
-        bt = max_over_ranks(time.perf_counter() - t0)
-        bk = max_over_ranks(tv.option(fold.FOLD_OPT_KERNEL_NS) / 1e9)
+        # one untimed call of the same batch sizes the context's buffers and device templates (a
+        # serving process's steady state); then the median of three timed calls
+        tv.batch(seqs)
+        bts, bks = [], []
+        for _ in range(3):
+            barrier_sync()
+            t0 = time.perf_counter()
+            res = tv.batch(seqs)
+            bts.append(time.perf_counter() - t0)
+            bks.append(tv.option(fold.FOLD_OPT_KERNEL_NS) / 1e9)
+        bt = max_over_ranks(statistics.median(bts))
+        bk = max_over_ranks(statistics.median(bks))
         # one-at-a-time baseline on a 1-in-16 sample, device-timed, scaled to all sequences
         sample = seqs[::16]
         loop_s = 0.0
@@ -507,6 +513,7 @@ def main():
                  "seq_per_s_one_at_a_time": len(seqs) / loop_s,   # this rank's share on one GPU
                  "speedup_vs_one_at_a_time": (loop_s / bk) if bk > 0 else None,
                  "one_at_a_time_sample": "device time of every 16th sequence, scaled to 4096",
+                 "timing": "median of 3 calls after one untimed call of the same batch",
                  "total_cells": int(sum(metrics.cells(len(s)) for s in seqs)), "checksum": int(res.sum())}
 
     # ---- serving: Poisson arrivals, lengths log-uniform in [50, 8000], 60 GB D budget
