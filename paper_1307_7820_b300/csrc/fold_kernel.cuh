@@ -1343,7 +1343,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             ws.y[(T - 1) & 1][yslot] = (int16_t)(bv + (int)((pbn >> (T - 1)) & 1u));
         }
         __syncwarp();
-#pragma unroll 1
+#pragma unroll 2
         for (int r = T - 1; r >= 0; --r) {
             // the closure's inputs go out first; the work below fills their latency
             const uint4 *yp = reinterpret_cast<const uint4 *>(ws.y[r & 1]);
