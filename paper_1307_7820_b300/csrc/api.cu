@@ -948,6 +948,12 @@ int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int3
         if (lens[k] < 0 || lens[k] > FOLD_MAX_N || (lens[k] > 0 && !seqs[k])) return FOLD_EINVAL;
     cudaSetDevice(ctx->device);
     Plan pl = make_plan(lens, count, ctx->q, ctx->method);
+    cudaStream_t st = ctx->stream;
+    // the workspace's zeroed part is cleared on the device while the host builds the rest
+    if (ensure_buf(ctx->ws, pl.bytes)) return FOLD_ENOMEM;
+    uint8_t *ws = reinterpret_cast<uint8_t *>(ctx->ws.ptr);
+    cudaError_t e = cudaMemsetAsync(ws, 0, pl.zero_bytes, st);
+    if (e != cudaSuccess) return status_from_cuda(e);
     int maxNT = 0;
     for (int v : pl.NTs) maxNT = std::max(maxNT, v);
     // a batch is bound by throughput, not by one fold's critical path: chunks of kc blocks each
@@ -959,7 +965,6 @@ int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int3
     std::vector<ScheduleSeg> segs;
     const size_t ntasks = schedule_segments(pl.NTs, kc, strip, !flat, tpls, segs);
     if (ntasks > (size_t)INT32_MAX) return FOLD_EINVAL;
-    cudaStream_t st = ctx->stream;
     // the task list is gathered on the device from device copies of the per-size templates (only
     // the segment list crosses the bus) when they fit the store; else it is built here
     std::vector<size_t> tfirst;
@@ -1011,16 +1016,13 @@ int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int3
         build_schedule_into(pl.NTs, kc, strip, !flat, hlist, ntasks);
     }
     int32_t *hres = reinterpret_cast<int32_t *>(h + codes_bytes + sd_bytes + list_bytes);
-    if (ensure_buf(ctx->ws, pl.bytes) || ensure_buf(ctx->aux, sd_bytes + task_bytes + res_bytes + seg_bytes))
-        return FOLD_ENOMEM;
-    uint8_t *ws = reinterpret_cast<uint8_t *>(ctx->ws.ptr);
+    if (ensure_buf(ctx->aux, sd_bytes + task_bytes + res_bytes + seg_bytes)) return FOLD_ENOMEM;
     uint8_t *aux = reinterpret_cast<uint8_t *>(ctx->aux.ptr);
     SeqDesc *d_sd = reinterpret_cast<SeqDesc *>(aux);
     int4 *d_tasks = reinterpret_cast<int4 *>(aux + sd_bytes);
     int32_t *d_res = reinterpret_cast<int32_t *>(aux + sd_bytes + task_bytes);
     int4 *d_segs = reinterpret_cast<int4 *>(aux + sd_bytes + task_bytes + res_bytes);
-    cudaError_t e = cudaMemsetAsync(ws, 0, pl.zero_bytes, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ws + pl.off_codes, hcodes, codes_bytes, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(ws + pl.off_codes, hcodes, codes_bytes, cudaMemcpyHostToDevice, st);
     if (gather) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(aux, h + codes_bytes, sd_bytes, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_segs, hlist, segs.size() * sizeof(int4), cudaMemcpyHostToDevice, st);

@@ -208,11 +208,19 @@ size_t schedule_segments(const std::vector<int> &NTs, int kc, int strip, bool ge
         }
         tix[(size_t)q] = it->second;
     }
+    // within a step the sequences go longest first (a step's tasks depend only on earlier steps, so
+    // any order there keeps the list valid): the longest chains get their tasks first, and the scan
+    // of a step stops at the first sequence that has no tile diagonal t
+    std::vector<int> ord;
+    ord.reserve((size_t)nseq);
+    for (int q = 0; q < nseq; ++q)
+        if (tix[(size_t)q] >= 0) ord.push_back(q);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return NTs[a] > NTs[b]; });
     size_t k = 0;
     for (int t = 0; t < maxNT; ++t) {
         for (int part = 0; part < 2; ++part) {
-            for (int q = 0; q < nseq; ++q) {
-                if (tix[(size_t)q] < 0 || t >= NTs[q]) continue;
+            for (int q : ord) {
+                if (t >= NTs[q]) break;
                 const SeqTemplate *p = tpls[(size_t)tix[(size_t)q]].get();
                 const int a = part == 0 ? p->near_begin[t] : p->chunk_begin[t];
                 const int b = part == 0 ? p->chunk_begin[t] : p->near_begin[t + 1];

@@ -196,16 +196,24 @@ def fold_score_dev(ctx: int, d_codes: int, n: int, d_ws: int, ws_bytes: int, d_m
 def fold_batch(ctx: int, seqs, want_D: bool = False):
     bs = [s.encode("ascii") for s in seqs]
     k = len(bs)
-    arr = (ctypes.c_char_p * k)(*bs)
-    lens = (ctypes.c_int32 * k)(*[len(x) for x in bs])
-    out = (ctypes.c_int32 * k)()
+    # one buffer holds every sequence; the pointer array points into it (kept alive by `blob`)
+    blob = b"".join(bs)
+    lens = np.fromiter((len(x) for x in bs), dtype=np.int32, count=k)
+    offs = np.zeros(k, dtype=np.uint64)
+    if k > 1:
+        np.cumsum(lens[:-1], dtype=np.uint64, out=offs[1:])
+    base = ctypes.cast(ctypes.c_char_p(blob), ctypes.c_void_p).value or 0
+    ptrs = offs + np.uint64(base)
+    out = np.zeros(max(k, 1), dtype=np.int32)
     Ds = None
     dptr = None
     if want_D:
         Ds = [np.zeros((len(x), len(x)), dtype=np.int16) for x in bs]
         dptr = (ctypes.c_void_p * k)(*[D.ctypes.data if D.size else None for D in Ds])
-    _check(lib().fold_batch(ctx, k, arr, lens, out, dptr), "fold_batch")
-    res = np.array(list(out), dtype=np.int32)
+    _check(lib().fold_batch(ctx, k, ptrs.ctypes.data_as(ctypes.POINTER(ctypes.c_char_p)),
+                            lens.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), dptr), "fold_batch")
+    res = out[:k].copy()
     return (res, Ds) if want_D else res
 
 
