@@ -159,6 +159,16 @@ int64_t fold_trace_copy(fold_ctx *ctx, fold_trace_rec *out, int64_t cap);
  * or a tile count above 2048). */
 int fold_schedule_check(int32_t n, int q, int method, int32_t kchunk);
 
+/* Host-only check of the interleaved list fold_batch builds for `count`
+ * sequences of lengths lens[] (fixed chunks of kchunk blocks, 0 = 64, as
+ * fold_batch by default): every task carries a sequence index below count, and
+ * each sequence's tasks appear exactly in the order of its single-sequence list,
+ * which fold_schedule_check validates; so each sequence waits only on its own
+ * earlier tasks; each distinct size's list is checked as by fold_schedule_check.
+ * Returns 0 if valid, a positive failure code otherwise, or -FOLD_EINVAL for bad
+ * arguments (a length above 65535 or a tile count above 512). */
+int fold_batch_schedule_check(int32_t count, const int32_t *lens, int q, int method, int32_t kchunk);
+
 /* Copies the R table to host memory: out[(h << (q-1)) | c] = R(h,c) for the
  * (q-1)-bit horizontal vector h and vertical vector c (bit p-1 holds
  * difference p; vertical differences stored as positive bits).  cap is the

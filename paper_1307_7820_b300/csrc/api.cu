@@ -811,6 +811,49 @@ int fold_schedule_check(int32_t n, int q, int method, int32_t kchunk) {
     return check_schedule(NT, kc, strip_of(q, method), tv);
 }
 
+int fold_batch_schedule_check(int32_t count, const int32_t *lens, int q, int method, int32_t kchunk) {
+    if (count < 0 || (count > 0 && !lens) || q < 2 || q > 10 ||
+        (method != FOLD_METHOD_TWO_VECTOR && method != FOLD_METHOD_PLAIN) || kchunk < 0)
+        return -FOLD_EINVAL;
+    const int T = tile_of(q, method), strip = strip_of(q, method);
+    const int kc = kchunk > 0 ? kchunk : 64;
+    std::vector<int> nts((size_t)count);
+    for (int k = 0; k < count; ++k) {
+        if (lens[k] < 0 || lens[k] > FOLD_MAX_N) return -FOLD_EINVAL;
+        nts[(size_t)k] = (lens[k] + T - 1) / T;
+        if (nts[(size_t)k] > 512) return -FOLD_EINVAL;   // the check keeps NT^3 counters per size
+    }
+    // every distinct size's own list is valid (coverage, chunk counts, dependency order)
+    std::vector<char> checked(513, 0);
+    for (int v : nts) {
+        if (v == 0 || checked[(size_t)v]) continue;
+        checked[(size_t)v] = 1;
+        const int rc = check_schedule(v, kc, strip, seq_template(v, kc, strip, false)->tasks);
+        if (rc) return 10 + rc;
+    }
+    std::vector<int4> all;
+    build_schedule(nts, kc, strip, all, false);
+    // each sequence's tasks, in list order, must be its own list
+    std::vector<std::vector<int4>> per((size_t)count);
+    for (const int4 &t : all) {
+        if (t.x < 0 || t.x >= count) return 1;
+        per[(size_t)t.x].push_back(t);
+    }
+    for (int k = 0; k < count; ++k) {
+        if (nts[(size_t)k] == 0) {
+            if (!per[(size_t)k].empty()) return 2;
+            continue;
+        }
+        const std::vector<int4> &own = seq_template(nts[(size_t)k], kc, strip, false)->tasks;
+        if (own.size() != per[(size_t)k].size()) return 3;
+        for (size_t e = 0; e < own.size(); ++e) {
+            const int4 a = own[e], b = per[(size_t)k][e];
+            if (a.y != b.y || a.z != b.z || a.w != b.w) return 4;
+        }
+    }
+    return 0;
+}
+
 int fold_rtable(fold_ctx *ctx, uint8_t *out, int64_t cap) {
     if (!ctx || !out) return FOLD_EINVAL;
     int64_t nent = (int64_t)1 << (2 * (ctx->q - 1));

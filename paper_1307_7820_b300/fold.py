@@ -34,7 +34,7 @@ ABI_SYMBOLS = (
     "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop", "fold_serve_stats_get",
     "fold_serve_warm",
     "fold_trace_copy",
-    "fold_score_static", "fold_schedule_check", "fold_tune", "fold_tune_q", "fold_tune_save", "fold_tune_load",
+    "fold_score_static", "fold_schedule_check", "fold_batch_schedule_check", "fold_tune", "fold_tune_q", "fold_tune_save", "fold_tune_load",
     "fold_structure", "fold_structure_workspace_bytes", "fold_structure_dev",
 )
 
@@ -113,6 +113,8 @@ def lib():
     L.fold_score_static.restype = ctypes.c_int
     L.fold_schedule_check.argtypes = [i32, ctypes.c_int, ctypes.c_int, i32]
     L.fold_schedule_check.restype = ctypes.c_int
+    L.fold_batch_schedule_check.argtypes = [i32, P(i32), ctypes.c_int, ctypes.c_int, i32]
+    L.fold_batch_schedule_check.restype = ctypes.c_int
     L.fold_trace_copy.restype = i64
     L.fold_structure.argtypes = [vp, ctypes.c_char_p, i32, P(i32), vp, vp]
     L.fold_structure.restype = ctypes.c_int
@@ -232,6 +234,13 @@ def fold_score_static(d_codes: int | None, n: int, pair_mask: int, d_max_pairs: 
                       d_D_out: int | None = None, stream: int | None = None) -> None:
     """Allocation-free fold of up to FOLD_STATIC_MAX_N bases (device pointers as ints)."""
     _check(lib().fold_score_static(d_codes, n, pair_mask, d_max_pairs, d_D_out, stream), "fold_score_static")
+
+
+def fold_batch_schedule_check(lens, q: int = 8, method: int = FOLD_METHOD_TWO_VECTOR, kchunk: int = 0) -> int:
+    """Host check of fold_batch's interleaved list for these lengths (0 = valid)."""
+    arr = np.ascontiguousarray(lens, dtype=np.int32)
+    return lib().fold_batch_schedule_check(len(arr), arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), q, method,
+                                           kchunk)
 
 
 def fold_schedule_check(n: int, q: int = 8, method: int = FOLD_METHOD_TWO_VECTOR, kchunk: int = 0) -> int:

@@ -33,6 +33,18 @@ def test_schedule_valid_chunk_sizes(kchunk):
         assert fold.fold_schedule_check(n, 8, fold.FOLD_METHOD_PLAIN, kchunk) == 0
 
 
+@pytest.mark.parametrize("method", [fold.FOLD_METHOD_TWO_VECTOR, fold.FOLD_METHOD_PLAIN])
+def test_batch_list_valid(method):
+    # fold_batch's interleaved list (longest sequence first within a step): each sequence's tasks in
+    # its own list's order, every distinct size's list valid
+    from paper_1307_7820_b300 import synth
+    lens = [len(s) for s in synth.batch(300, 1, 3000, 31)] + [0, 1, 32, 33, 3000, 3000]
+    assert fold.fold_batch_schedule_check(lens, 8, method, 0) == 0
+    assert fold.fold_batch_schedule_check(lens[:7], 8, method, 3) == 0
+    assert fold.fold_batch_schedule_check([], 8, method, 0) == 0
+    assert fold.fold_batch_schedule_check([65536], 8, method, 0) == -fold.FOLD_EINVAL
+
+
 def test_schedule_check_rejects_bad_arguments():
     assert fold.fold_schedule_check(-1, 8, 0, 0) == -fold.FOLD_EINVAL
     assert fold.fold_schedule_check(100, 11, 0, 0) == -fold.FOLD_EINVAL
