@@ -208,7 +208,11 @@ int fold_score_dev(fold_ctx *ctx, const uint8_t *d_codes, int32_t n, void *d_ws,
 /* Folds `count` sequences in one persistent launch (sequence-level and
  * wavefront parallelism together).  seqs[k] has lens[k] letters;
  * max_pairs_out[k] receives D_k(0,n_k-1); D_out may be NULL, and so may any
- * D_out[k] (else lens[k]*lens[k] int16).  Synchronous. */
+ * D_out[k] (else lens[k]*lens[k] int16).  Synchronous.  Returns FOLD_EINVAL
+ * for a letter outside ACGU/acgu (nothing is folded).  The context keeps its
+ * workspace, a pinned staging buffer and (FOLD_OPT_BATCH_GATHER) device copies
+ * of the per-size task templates, up to 1 GiB, between calls; they are freed
+ * by fold_destroy. */
 int fold_batch(fold_ctx *ctx, int32_t count, const char *const *seqs, const int32_t *lens,
                int32_t *max_pairs_out, int16_t *const *D_out);
 
