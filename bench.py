@@ -285,7 +285,7 @@ def serve_bench(f, rates, seconds, dev, stream, torch, fold, metrics, synth):
                     "throughput_cells_s": cells / wall,
                     "one_at_a_time_req_s": count / alone_s,
                     "one_at_a_time_note": "device time of every request folded alone, back to back",
-                    "slices": st["slices"], "tasks_per_slice": st["tasks"] / max(1, st["slices"]),
+                    "slices": st["slices"], "solo": st["solo"], "tasks_per_slice": st["tasks"] / max(1, st["slices"]),
                     "gpu_busy": st["gpu_ms"] / (1e3 * wall), "host_prep_ms": st["prep_ms"],
                     "lengths": "log-uniform [50, 8000]; 80% uniform, 10% GC-rich, 10% structured",
                     "budget_bytes": budget, "warm_s": warm_s})

@@ -336,6 +336,9 @@ typedef struct fold_serve_stats {
     double prep_ms;         /* host time gathering slices' task lists and descriptors */
     int32_t queued;         /* waiting for admission now */
     int32_t inflight;       /* on the device now */
+    uint64_t solo;          /* requests that arrived to an idle server (nothing else in flight or
+                               waiting, length <= 8192) and were folded in one launch with the
+                               single-fold work split instead of slice by slice */
 } fold_serve_stats;
 /* FOLD_EINVAL if ctx or out is NULL or no serving loop runs. */
 int fold_serve_stats_get(fold_ctx *ctx, fold_serve_stats *out);

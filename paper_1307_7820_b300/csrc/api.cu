@@ -364,19 +364,21 @@ int single_schedule(fold_ctx *ctx, int n, const Plan &pl, const int4 **tasks, in
                     bool *layout_ok, const SeqDesc **d_sd, bool capturing) {
     int NT = pl.NTs[0];
     const FoldOpts o = single_opts(ctx, n);
+    const bool drop = ctx->test_drop_task != 0;
     int kc = o.kc > 0 ? o.kc : kc_auto(NT);
     // the split list is the same for every split layout; layout_ok is assumed for the choice here
     const int nearc = plan_split(ctx, o, NT, grid_for(ctx), true).near_ctas;
     long long key = ((((long long)n << 24) | ((long long)ctx->method << 20) | ((long long)ctx->q << 16) | kc) << 12) |
                     (nearc & 0xfff);
-    if (ctx->test_drop_task) key = -key - 1;   // separate cache entry for the fault-injection schedule
+    if (drop) key = -key - 1;   // separate cache entry for the fault-injection schedule
+    std::lock_guard<std::mutex> lk(ctx->sched_mu);
     auto it = ctx->sched_cache.find(key);
     if (it == ctx->sched_cache.end()) {
         // building the list allocates and copies synchronously: not while a stream is being captured
         if (capturing) return FOLD_EINVAL;
         std::vector<int4> tv;
         build_schedule(pl.NTs, kc, strip_of(ctx->q, ctx->method), tv);
-        if (ctx->test_drop_task) {
+        if (drop) {
             // host-side fault injection: drop the NEAR task of tile (0,1)
             for (size_t k = 0; k < tv.size(); ++k)
                 if (task_type(tv[k].y) == kTaskNear && task_I(tv[k].y) == 0 && task_J(tv[k].y) == 1) {

@@ -6,6 +6,7 @@
 
 #include <map>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "fold_common.h"
@@ -77,7 +78,8 @@ struct fold_ctx {
     uint8_t *d_rcanon = nullptr;
     uint8_t *d_rpacked_buf = nullptr;
     const uint8_t *d_rpacked = nullptr;
-    std::map<long long, fold::CachedSched> sched_cache;
+    std::map<long long, fold::CachedSched> sched_cache;   // guarded by sched_mu
+    std::mutex sched_mu;
     fold::DevBuf ws, aux, dout;
     fold::HostBuf hstage;
     // device copies of the task templates fold_batch gathers its list from: the templates (held, so
@@ -115,6 +117,7 @@ int enqueue_single(fold_ctx *ctx, const uint8_t *d_codes, int n, uint8_t *ws, si
                    int16_t *d_D, cudaStream_t st);
 int split_queues(std::vector<int4> &tasks);
 bool encode_seq(const char *seq, int n, uint8_t *out);
+
 int ensure_buf(DevBuf &b, size_t bytes);
 int ensure_host(HostBuf &b, size_t bytes);
 }  // namespace fold

@@ -37,6 +37,7 @@ namespace fold {
 constexpr int kSliceMin = 2;         // tile diagonals per request per launch: adapted so that one
 constexpr int kSliceMax = 64;        // launch takes about kSliceTargetMs
 constexpr double kSliceTargetMs = 2.0;
+constexpr int kSoloMaxN = 8192;      // a lone request up to this length folds in one launch (~3.5 ms)
 constexpr size_t kMaxQueued = 1 << 20;
 constexpr size_t kLaunchBytes0 = size_t(16) << 20;   // initial launch-list buffers (host and device)
 
@@ -190,6 +191,99 @@ static void serve_loop(ServeState *S) {
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(base + r->pl.off_codes, r->codes.data(), r->codes.size(), cudaMemcpyHostToDevice, S->st);
             // the host copy of the codes must stay alive until this copy ran: synchronised below
+        }
+        // a request alone in the system (just admitted, nothing else in flight or waiting) folds in
+        // one launch with the single-fold work split (column mode where it applies), as
+        // fold_score_dev would, instead of slice by slice in the one-queue layout; up to
+        // kSoloMaxN, so that a request arriving meanwhile waits at most about that fold's time
+        bool solo = false;
+        if (e == cudaSuccess && active.size() == 1 && admitted.size() == 1 && active[0]->cursor == 0 &&
+            active[0]->n >= 2 && active[0]->n <= kSoloMaxN) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            solo = S->queued.empty();
+        }
+        if (solo) {
+            Request &r = *active[0];
+            const SeqTemplate &sc = *r.sched;
+            const FoldOpts o;   // automatic work split, whatever the caller's options
+            const SplitPlan sp = plan_split(ctx, o, r.NT, grid_for(ctx), true);
+            const size_t nt = sc.tasks.size();
+            // launch buffers: SeqDesc | result | tasks; with tile-only CTAs the list is split into
+            // [tile tasks | chunks], each in the template's order (its tiles are by diagonal, as
+            // column mode reads them): both parts are whole ranges of every step
+            const size_t o_res = 256, o_tasks = 512, need = al256(o_tasks + sizeof(int4) * nt);
+            if (ensure_buf(S->d_launch, grown(S->d_launch.bytes, need)) == FOLD_OK &&
+                ensure_host(S->h_launch, grown(S->h_launch.bytes, need)) == FOLD_OK) {
+                uint8_t *h = reinterpret_cast<uint8_t *>(S->h_launch.ptr);
+                uint8_t *d = reinterpret_cast<uint8_t *>(S->d_launch.ptr);
+                memcpy(h, &r.pl.sd[0], sizeof(SeqDesc));
+                int4 *dst = reinterpret_cast<int4 *>(h + o_tasks);
+                int nnear = 0;
+                if (sp.near_ctas > 0) {
+                    for (int t = 0; t < r.NT; ++t) {
+                        const int a = sc.near_begin[t], b = sc.chunk_begin[t];
+                        memcpy(dst, sc.tasks.data() + a, sizeof(int4) * (size_t)(b - a));
+                        dst += b - a;
+                        nnear += b - a;
+                    }
+                    for (int t = 0; t < r.NT; ++t) {
+                        const int a = sc.chunk_begin[t], b = sc.near_begin[t + 1];
+                        memcpy(dst, sc.tasks.data() + a, sizeof(int4) * (size_t)(b - a));
+                        dst += b - a;
+                    }
+                } else {
+                    memcpy(dst, sc.tasks.data(), sizeof(int4) * nt);
+                }
+                if (e == cudaSuccess) e = cudaMemcpyAsync(d, h, sizeof(SeqDesc), cudaMemcpyHostToDevice, S->st);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(d + o_tasks, h + o_tasks, sizeof(int4) * nt, cudaMemcpyHostToDevice, S->st);
+                FoldParams p = make_params(ctx, r.pl, S->arena_base + r.block, reinterpret_cast<const int4 *>(d + o_tasks),
+                                           (int)nt, reinterpret_cast<const SeqDesc *>(d));
+                if (sp.near_ctas > 0) {
+                    p.col_mode = sp.col_mode;
+                    p.cols_per_cta = sp.cpc;
+                    p.nnear = nnear;
+                    p.near_ctas = sp.near_ctas;
+                }
+                int32_t *d_out = reinterpret_cast<int32_t *>(d + o_res);
+                int32_t *h_out = reinterpret_cast<int32_t *>(h + o_res);
+                const auto t_launch = std::chrono::steady_clock::now();
+                if (e == cudaSuccess) e = cudaEventRecord(S->ev0, S->st);
+                if (e == cudaSuccess) e = launch_fold(p, ctx->q, ctx->method, grid_for(ctx), S->st);
+                if (e == cudaSuccess) e = launch_finalize(p.error, p.results, 1, d_out, S->st);
+                if (e == cudaSuccess) e = cudaEventRecord(S->ev1, S->st);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, d_out, sizeof(int32_t), cudaMemcpyDeviceToHost, S->st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
+                S->launches += 2;
+                const auto t_done = std::chrono::steady_clock::now();
+                float gpu_ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&gpu_ms, S->ev0, S->ev1);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    fail_inflight(S, FOLD_ECUDA);
+                    continue;
+                }
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->stats.slices++;
+                S->stats.solo++;
+                S->stats.tasks += (uint64_t)nt;
+                S->stats.admitted += 1;
+                S->stats.gpu_ms += gpu_ms;
+                S->stats.slice_ms += std::chrono::duration<double, std::milli>(t_done - t_prep).count();
+                S->stats.prep_ms += std::chrono::duration<double, std::milli>(t_launch - t_prep).count();
+                S->stats.finished++;
+                if (h_out[0] < 0) {   // a bounded device-side wait expired
+                    r.state = 3;
+                    r.status = -h_out[0] == FOLD_ETIMEOUT ? FOLD_ETIMEOUT : FOLD_ECUDA;
+                } else {
+                    r.state = 2;
+                    r.result = h_out[0];
+                }
+                r.cursor = r.NT;
+                S->inflight.clear();
+                continue;
+            }
+            // no room for the launch buffers: slices as for any request
         }
         // one slice: `slice` steps of every active request, interleaved step by step, gathered
         // straight into the pinned staging buffer (whole steps are contiguous in a template)

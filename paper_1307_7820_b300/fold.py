@@ -62,7 +62,8 @@ class ServeStats(ctypes.Structure):
     """struct fold_serve_stats"""
     _fields_ = [("slices", ctypes.c_uint64), ("tasks", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
                 ("finished", ctypes.c_uint64), ("gpu_ms", ctypes.c_double), ("slice_ms", ctypes.c_double),
-                ("prep_ms", ctypes.c_double), ("queued", ctypes.c_int32), ("inflight", ctypes.c_int32)]
+                ("prep_ms", ctypes.c_double), ("queued", ctypes.c_int32), ("inflight", ctypes.c_int32),
+                ("solo", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -58,6 +58,33 @@ def test_serve_mix_equals_alone():
         f.close()
 
 
+def test_serve_lone_requests_fold_in_one_launch():
+    # each request arrives to an idle server: up to 8192 long it folds in one launch with the single
+    # fold's work split (stats "solo"), longer ones slice by slice; scores and tables as alone
+    f = fold.Folder(q=8)
+    try:
+        seqs = [synth.uniform(2, 51), synth.gc_rich(33, 52), synth.structured(700, 53), synth.uniform(3000, 54),
+                synth.uniform(8192, 55), synth.gc_rich(9000, 56)]
+        alone = [f.score(s) for s in seqs]
+        fold.fold_serve_start(f.ctx, 8 << 30, 64)
+        for k, s in enumerate(seqs):
+            t = fold.fold_serve_submit(f.ctx, s)
+            D = np.zeros((len(s), len(s)), dtype=np.int16) if len(s) <= 700 else None
+            r = _drain(f.ctx, [t], want_D={t: D} if D is not None else None)[t]
+            assert r == alone[k]
+            if D is not None:
+                ref = oracle.nussinov(s)
+                assert r == ref[0, len(s) - 1]
+                assert np.array_equal(D.astype(np.int32), ref)
+        st = fold.fold_serve_stats(f.ctx)
+        assert st["solo"] == 5
+        assert st["admitted"] == st["finished"] == len(seqs)
+        assert st["slices"] > st["solo"]   # the 9000-long one took several launches
+    finally:
+        fold.fold_serve_stop(f.ctx)
+        f.close()
+
+
 def test_serve_budget_admission_and_tables():
     f = fold.Folder(q=8)
     try:
