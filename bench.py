@@ -230,7 +230,7 @@ def serve_bench(f, rates, seconds, dev, stream, torch, fold, metrics, synth):
         fold.fold_serve_start(f.ctx, budget, 4096)
         submit_t = {}
         done_t = {}
-        tickets = [None] * count
+        t2k = {}   # ticket -> request index, written by the submitter
         t0 = time.perf_counter()
 
         def submitter():
@@ -240,7 +240,7 @@ def serve_bench(f, rates, seconds, dev, stream, torch, fold, metrics, synth):
                 submit_t[k] = time.perf_counter()
                 while True:
                     try:
-                        tickets[k] = fold.fold_serve_submit(f.ctx, s)
+                        t2k[fold.fold_serve_submit(f.ctx, s)] = k
                         break
                     except fold.FoldError as e:
                         if e.code != fold.FOLD_EAGAIN:
@@ -249,18 +249,20 @@ def serve_bench(f, rates, seconds, dev, stream, torch, fold, metrics, synth):
 
         th = threading.Thread(target=submitter)
         th.start()
-        pending = set(range(count))
         results = {}
-        while pending:
-            for k in list(pending):
-                if tickets[k] is None:
+        seen = {}   # finished tickets -> time reported (kept until the submitter has recorded them)
+        while len(results) < count:
+            # blocks (GIL released) until the server reports a finished request
+            t = fold.fold_serve_wait_any(f.ctx, 50)
+            if t is not None:
+                seen[t] = time.perf_counter()
+            for t, tdone in list(seen.items()):
+                k = t2k.get(t)
+                if k is None:
                     continue
-                r = fold.fold_serve_poll(f.ctx, tickets[k])
-                if r is not None:
-                    done_t[k] = time.perf_counter()
-                    results[k] = r
-                    pending.discard(k)
-            time.sleep(0.0002)
+                results[k] = fold.fold_serve_poll(f.ctx, t)
+                done_t[k] = tdone
+                del seen[t]
         th.join()
         wall = max(done_t.values()) - t0
         st = fold.fold_serve_stats(f.ctx)

@@ -29,8 +29,8 @@
  *   - the context owns its device state; the caller owns every buffer it
  *     passes, and inputs are not retained after a call returns (serve_submit
  *     copies the sequence);
- *   - a context is used by one thread at a time, except fold_serve_submit and
- *     fold_serve_poll, which are thread-safe.
+ *   - a context is used by one thread at a time, except fold_serve_submit,
+ *     fold_serve_poll and fold_serve_wait_any, which are thread-safe.
  */
 #ifndef FOLD_B300_H
 #define FOLD_B300_H
@@ -314,6 +314,13 @@ int fold_serve_start(fold_ctx *ctx, int64_t budget_bytes, int32_t max_inflight);
 int fold_serve_submit(fold_ctx *ctx, const char *seq, int32_t n, uint64_t *ticket);
 int fold_serve_poll(fold_ctx *ctx, uint64_t ticket, int32_t *max_pairs, int16_t *D_out);
 int fold_serve_stop(fold_ctx *ctx);
+
+/* Blocks until a request has finished (done or failed) that this call has not
+ * reported yet, for at most timeout_ms: FOLD_OK with its ticket (collect it with
+ * fold_serve_poll), FOLD_ENOTREADY on timeout, FOLD_EINVAL if no serving loop
+ * runs.  Tickets already collected by fold_serve_poll are skipped.  Every call
+ * must have returned before fold_serve_stop. */
+int fold_serve_wait_any(fold_ctx *ctx, int32_t timeout_ms, uint64_t *ticket);
 
 /* Builds now, on up to 16 host threads, the task lists the serving loop (and
  * single folds) of this context use for every sequence length up to max_n:

@@ -104,6 +104,8 @@ struct ServeState {
     std::condition_variable cv;
     std::deque<uint64_t> queued;
     std::vector<uint64_t> inflight;
+    std::deque<uint64_t> done_q;     // finished tickets not yet reported by fold_serve_wait_any
+    std::condition_variable done_cv;
     std::unordered_map<uint64_t, Request> reqs;
     uint64_t next_ticket = 1;
     bool stop = false;
@@ -138,6 +140,12 @@ static SeqDesc arena_desc(const Request &r, int slot) {
     return d;
 }
 
+// a request is done or failed (S->mu held): report it to fold_serve_wait_any
+static void mark_done(ServeState *S, uint64_t ticket) {
+    S->done_q.push_back(ticket);
+    S->done_cv.notify_all();
+}
+
 static void fail_inflight(ServeState *S, int status) {
     std::lock_guard<std::mutex> lk(S->mu);
     for (uint64_t t : S->inflight) {
@@ -146,6 +154,7 @@ static void fail_inflight(ServeState *S, int status) {
         it->second.state = 3;
         it->second.status = status;
         S->stats.finished++;
+        mark_done(S, t);
     }
     S->inflight.clear();
 }
@@ -280,6 +289,7 @@ static void serve_loop(ServeState *S) {
                     r.result = h_out[0];
                 }
                 r.cursor = r.NT;
+                mark_done(S, r.ticket);
                 S->inflight.clear();
                 continue;
             }
@@ -386,6 +396,7 @@ static void serve_loop(ServeState *S) {
                 S->stats.finished++;
                 r.state = 3;
                 r.status = -hres[k] == FOLD_ETIMEOUT ? FOLD_ETIMEOUT : FOLD_ECUDA;
+                mark_done(S, r.ticket);
                 continue;
             }
             r.cursor += used;
@@ -393,6 +404,7 @@ static void serve_loop(ServeState *S) {
                 r.state = 2;
                 r.result = r.n >= 2 ? hres[k] : 0;
                 S->stats.finished++;
+                mark_done(S, r.ticket);
             } else {
                 still.push_back(r.ticket);
             }
@@ -472,7 +484,9 @@ int fold_serve_submit(fold_ctx *ctx, const char *seq, int32_t n, uint64_t *ticke
     if (n == 0) {
         r.state = 2;
         r.result = 0;
-        S->reqs.emplace(r.ticket, std::move(r));
+        const uint64_t t0 = r.ticket;
+        S->reqs.emplace(t0, std::move(r));
+        mark_done(S, t0);
         return FOLD_OK;
     }
     uint64_t t = r.ticket;
@@ -480,6 +494,26 @@ int fold_serve_submit(fold_ctx *ctx, const char *seq, int32_t n, uint64_t *ticke
     S->queued.push_back(t);
     S->cv.notify_one();
     return FOLD_OK;
+}
+
+int fold_serve_wait_any(fold_ctx *ctx, int32_t timeout_ms, uint64_t *ticket) {
+    if (!ctx || !ticket || timeout_ms < 0) return FOLD_EINVAL;
+    ServeState *S = ctx->serve;
+    if (!S) return FOLD_EINVAL;
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        while (!S->done_q.empty()) {
+            const uint64_t t = S->done_q.front();
+            S->done_q.pop_front();
+            if (S->reqs.count(t)) {   // tickets already polled are skipped
+                *ticket = t;
+                return FOLD_OK;
+            }
+        }
+        if (S->done_cv.wait_until(lk, deadline) == std::cv_status::timeout && S->done_q.empty())
+            return FOLD_ENOTREADY;
+    }
 }
 
 int fold_serve_poll(fold_ctx *ctx, uint64_t ticket, int32_t *max_pairs, int16_t *D_out) {

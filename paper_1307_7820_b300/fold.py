@@ -32,7 +32,7 @@ ABI_SYMBOLS = (
     "fold_init", "fold_destroy", "fold_strerror", "fold_set_option", "fold_get_option", "fold_rtable",
     "fold_score", "fold_workspace_bytes", "fold_score_dev", "fold_batch",
     "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop", "fold_serve_stats_get",
-    "fold_serve_warm",
+    "fold_serve_warm", "fold_serve_wait_any",
     "fold_trace_copy",
     "fold_score_static", "fold_schedule_check", "fold_batch_schedule_check", "fold_tune", "fold_tune_q", "fold_tune_save", "fold_tune_load",
     "fold_structure", "fold_structure_workspace_bytes", "fold_structure_dev",
@@ -109,6 +109,8 @@ def lib():
     L.fold_serve_stop.argtypes = [vp]
     L.fold_serve_stats_get.argtypes = [vp, P(ServeStats)]
     L.fold_serve_warm.argtypes = [vp, i32]
+    L.fold_serve_wait_any.argtypes = [vp, i32, P(ctypes.c_uint64)]
+    L.fold_serve_wait_any.restype = ctypes.c_int
     L.fold_trace_copy.argtypes = [vp, vp, i64]
     L.fold_score_static.argtypes = [vp, i32, u16, vp, vp, vp]
     L.fold_score_static.restype = ctypes.c_int
@@ -306,6 +308,17 @@ def fold_serve_submit(ctx: int, seq: str) -> int:
     b = seq.encode("ascii")
     t = ctypes.c_uint64()
     _check(lib().fold_serve_submit(ctx, b, len(b), ctypes.byref(t)), "fold_serve_submit")
+    return t.value
+
+
+def fold_serve_wait_any(ctx: int, timeout_ms: int = 100) -> int | None:
+    """Ticket of a finished request not reported before (collect it with fold_serve_poll), or None
+    after timeout_ms."""
+    t = ctypes.c_uint64()
+    rc = lib().fold_serve_wait_any(ctx, timeout_ms, ctypes.byref(t))
+    if rc == FOLD_ENOTREADY:
+        return None
+    _check(rc, "fold_serve_wait_any")
     return t.value
 
 

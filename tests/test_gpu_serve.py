@@ -85,6 +85,29 @@ def test_serve_lone_requests_fold_in_one_launch():
         f.close()
 
 
+def test_serve_wait_any_reports_each_finished_request_once():
+    f = fold.Folder(q=8)
+    try:
+        fold.fold_serve_start(f.ctx, 8 << 30, 64)
+        assert fold.fold_serve_wait_any(f.ctx, 20) is None   # nothing submitted: times out
+        seqs = [synth.uniform(n, 70 + n) for n in (0, 5, 64, 400, 1500, 3000, 200)]
+        tickets = [fold.fold_serve_submit(f.ctx, s) for s in seqs]
+        got = {}
+        while len(got) < len(seqs):
+            t = fold.fold_serve_wait_any(f.ctx, 5000)
+            assert t is not None and t in tickets and t not in got
+            got[t] = fold.fold_serve_poll(f.ctx, t)
+        assert [got[t] for t in tickets] == [oracle.score(s) if len(s) else 0 for s in seqs]
+        # a ticket collected by poll before wait_any reports it is skipped
+        t = fold.fold_serve_submit(f.ctx, synth.uniform(300, 9))
+        while fold.fold_serve_poll(f.ctx, t) is None:
+            time.sleep(0.001)
+        assert fold.fold_serve_wait_any(f.ctx, 20) is None
+    finally:
+        fold.fold_serve_stop(f.ctx)
+        f.close()
+
+
 def test_serve_budget_admission_and_tables():
     f = fold.Folder(q=8)
     try:
