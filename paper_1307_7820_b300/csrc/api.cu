@@ -119,18 +119,17 @@ int grid_for(fold_ctx *ctx) {
 // Work split of a single fold.  Tile tasks form the critical path (one per tile diagonal, each
 // waiting for its neighbours); chunk tasks are throughput work.  Chunk warps on an SM slow the
 // tile warps there (issue slots, shared memory), so tile tasks may get SMs of their own.  The
-// candidate layouts, with the measured cost of one tile-diagonal step (B300, q = 8, two-vector;
-// the plain kernel's earlier figures in brackets):
-//   one shared queue                          about 20 us (16.5), chunks on every SM
-//   tile-only CTAs taking tile tasks          about 13 us (13.8), chunks on the other SMs
-//   column mode, 4 columns per tile CTA       about 9.9 us (13.0)
-//   column mode, 8 columns per tile CTA       about 12.5 us (15.0)
+// candidate layouts, with the measured cost of one tile-diagonal step (B300, q = 8):
+//   one shared queue                          about 20 us, chunks on every SM
+//   tile-only CTAs taking tile tasks          about 13 us, chunks on the other SMs
+//   column mode, 4 columns per tile CTA       about 9.9 us
+//   column mode, 8 columns per tile CTA       about 12.5 us
 // Column mode gives every tile column a warp of its own that computes it bottom-up: a tile's
 // bottom neighbour is the warp's previous tile, and its left neighbour comes through shared memory
 // unless it is the first column of its CTA.  A layout's time is modelled as the larger of the path
 // (NT steps) and the chunk work at the measured rates (two-vector about 4.3e9 lookups per ms,
-// plain about 2e10 split points per ms, on 148 SMs) spread over the SMs left to chunks (two-vector
-// chunk-only SMs at 1/0.86 of that rate); the fastest wins.
+// plain about 1.77e10 split points per ms, on 148 SMs) spread over the SMs left to chunks
+// (chunk-only SMs at 1/0.86 of that rate); the fastest wins.
 // The options force a layout: FOLD_OPT_NEAR_CTAS (0 = one queue, k = k tile CTAs) and
 // FOLD_OPT_COLUMNS (0 = no column mode, v = column mode with v columns per tile CTA).
 // Size buckets of the tuned settings: four per doubling of n.
@@ -178,18 +177,16 @@ SplitPlan plan_split(fold_ctx *ctx, const FoldOpts &o, int NT, int grid, bool la
     }
     if (NT < 8 || grid < 12) return sp;
     const double n = (double)NT * tile_of(ctx->q, ctx->method);
-    const bool tv = ctx->method == kTwoVector;
     const double work_ms = (148.0 / std::max(1, ctx->sm_count)) *
-                           (tv ? n * n * n / (6.0 * ctx->q) / 4.3e9 : n * n * n / 6.0 / 2.0e10);
-    // chunk-only SMs look up faster than SMs that also run tiles (two-vector: ~1/0.86, measured)
-    const double chunk_only = tv ? 0.86 : 1.0;
+                           (ctx->method == kTwoVector ? n * n * n / (6.0 * ctx->q) / 4.3e9 : n * n * n / 6.0 / 1.77e10);
+    // chunk-only SMs get through their work ~1/0.86 faster than SMs that also run tiles (measured)
     auto model = [&](double step_us, int near) {
-        return std::max(NT * step_us * 1e-3, work_ms * grid / std::max(1, grid - near) * (near > 0 ? chunk_only : 1.0));
+        return std::max(NT * step_us * 1e-3, work_ms * grid / std::max(1, grid - near) * (near > 0 ? 0.86 : 1.0));
     };
-    // tile-diagonal step of each layout (two-vector, q = 8, measured on B300: n = 2000..16384
-    // folds picked the fastest layout, or one within 1 %; the plain kernel keeps earlier figures)
-    const double step_one = tv ? 20.0 : 16.5, step_split = tv ? 13.0 : 13.8;
-    const double step_col[2] = {tv ? 9.9 : 13.0, tv ? 12.5 : 15.0};
+    // tile-diagonal step of each layout (q = 8, measured on B300; with these figures both kernels
+    // picked the fastest layout, or one within 1 %, at every size swept from n = 2000 to 16384)
+    const double step_one = 20.0, step_split = 13.0;
+    const double step_col[2] = {9.9, 12.5};
     double best = model(step_one, 0);
     const int near_split = std::max(2, std::min(ceil_div(NT, kWarpsPerCta), grid / 6));
     const double split = model(step_split, near_split);
