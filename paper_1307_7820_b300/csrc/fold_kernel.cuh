@@ -158,6 +158,28 @@ static __device__ __forceinline__ void red_max(int *p, int v) {
     asm volatile("red.relaxed.gpu.global.max.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Bulk reduction of a 16-byte-aligned shared buffer into global memory by the async proxy (one
+// instruction instead of one red per element); the shared source must be made visible to the async
+// proxy first (fence_proxy_async_smem by every writing thread), and the async proxy's global writes
+// must be fenced into the generic proxy (fence_proxy_async_global) before a release publishes them.
+static __device__ __forceinline__ void bulk_red_max_s32(int *gdst, const int *ssrc, unsigned bytes) {
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.max.s32 [%0], [%1], %2;"
+                 ::"l"(gdst), "r"((unsigned)__cvta_generic_to_shared(ssrc)), "r"(bytes) : "memory");
+}
+static __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the shared sources of every committed bulk operation have been read (they may be rewritten)
+static __device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// every committed bulk operation is complete
+static __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+static __device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+static __device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // 16-byte global -> shared copies that bypass L1 (both addresses 16-byte aligned)
 static __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -539,15 +561,40 @@ __device__ __forceinline__ long long run_far(const FoldParams &P, const SeqDesc 
     const long long tdone = P.trace ? (long long)gtimer() : 0;
     nt.start(lane);
     int *slot = P.pring + sd.p_off + ((size_t)((J - I) % kRing) * NT + I) * (T * T);
-    if (lane < T) {
+    if constexpr (WarpScratch<Q, M>::PB) {
+        // the partial maximum is staged in shared memory (pbuf shares its bytes with the chunk
+        // staging, free once the lookups are done) and merged by one bulk reduction; lane 0 waits
+        // for it, fences the async proxy's writes and publishes the count
+        __syncwarp();
+        if (lane < T) {
 #pragma unroll
-        for (int r = 0; r < T; ++r)
-            if (m[r] > 0) red_max(slot + r * T + lane, m[r]);
+            for (int r = 0; r < T; ++r) ws.pbuf[r * T + lane] = m[r];
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            bulk_red_max_s32(slot, ws.pbuf, (unsigned)(T * T * sizeof(int)));
+            bulk_commit();
+        }
+        nt.finish(lane);
+        if (lane == 0) {
+            bulk_wait_all();
+            fence_proxy_async_global();
+            __threadfence();
+            atomicAdd(P.cnt + sd.cnt_off + I * NT + J, 1);
+        }
+        __syncwarp();
+    } else {
+        if (lane < T) {
+#pragma unroll
+            for (int r = 0; r < T; ++r)
+                if (m[r] > 0) red_max(slot + r * T + lane, m[r]);
+        }
+        nt.finish(lane);
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicAdd(P.cnt + sd.cnt_off + I * NT + J, 1);
     }
-    nt.finish(lane);
-    __threadfence();
-    __syncwarp();
-    if (lane == 0) atomicAdd(P.cnt + sd.cnt_off + I * NT + J, 1);
     return tdone;
 }
 
@@ -685,6 +732,43 @@ __device__ __forceinline__ void far_strip_plain(const FoldParams &P, const SeqDe
     }
 }
 
+// A strip's partial maxima merged by bulk reductions: each tile's values (value(s2, r) for column
+// lane, row r) are staged in pbuf (free once the lookups are done: it shares its bytes with the chunk
+// staging) and reduced into the tile's P slot by one bulk operation; the next tile is staged once
+// the previous source has been read.  Lane 0 then waits for every reduction, fences the async
+// proxy's writes and publishes the tiles' counts.
+template <int Q, int M, int S, class V>
+__device__ __forceinline__ void merge_strip_bulk(const FoldParams &P, const SeqDesc &sd, int I, int J0, int Seff,
+                                                 WarpScratch<Q, M> &ws, int lane, NextTask &nt, V value) {
+    constexpr int T = Cfg<Q, M>::T;
+    const int NT = sd.NT;
+#pragma unroll
+    for (int s2 = 0; s2 < S; ++s2) {
+        if (s2 >= Seff) continue;
+        if (s2 > 0 && lane == 0) bulk_wait_read_all();
+        __syncwarp();
+        if (lane < T) {
+#pragma unroll
+            for (int r = 0; r < T; ++r) ws.pbuf[r * T + lane] = value(s2, r);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            int *slot = P.pring + sd.p_off + ((size_t)((J0 + s2 - I) % kRing) * NT + I) * (T * T);
+            bulk_red_max_s32(slot, ws.pbuf, (unsigned)(T * T * sizeof(int)));
+            bulk_commit();
+        }
+    }
+    nt.finish(lane);
+    if (lane == 0) {
+        bulk_wait_all();
+        fence_proxy_async_global();
+        __threadfence();
+        for (int s2 = 0; s2 < Seff; ++s2) atomicAdd(P.cnt + sd.cnt_off + I * NT + J0 + s2, 1);
+    }
+    __syncwarp();
+}
+
 template <int Q, int M, bool MEMO>
 __device__ __forceinline__ long long run_far_strip(const FoldParams &P, const SeqDesc &sd, int I, int J0, int Ka,
                                                    int Kb, WarpScratch<Q, M> &ws, const uint8_t *Rs, int lane,
@@ -713,6 +797,12 @@ __device__ __forceinline__ long long run_far_strip(const FoldParams &P, const Se
         far_strip_tv<Q, S, MEMO>(P, sd, I, J0, Seff, Ka, Kb, m2, ws, Rs, lane);
         if (P.trace) tdone = (long long)gtimer();
         nt.start(lane);
+        if constexpr (WarpScratch<Q, M>::PB) {
+            merge_strip_bulk<Q, M, S>(P, sd, I, J0, Seff, ws, lane, nt, [&](int s2, int r) {
+                return (s2 & 1) ? (int)(m2[s2 / 2][r] >> 16) : (int)(m2[s2 / 2][r] & 0xffffu);
+            });
+            return tdone;
+        }
         if (lane < T) {
 #pragma unroll
             for (int s2 = 0; s2 < S; ++s2) {
@@ -734,6 +824,11 @@ __device__ __forceinline__ long long run_far_strip(const FoldParams &P, const Se
         far_strip_plain<S>(P, sd, I, J0, Seff, Ka, Kb, acc, ws, lane);
         if (P.trace) tdone = (long long)gtimer();
         nt.start(lane);
+        if constexpr (WarpScratch<Q, M>::PB) {
+            merge_strip_bulk<Q, M, S>(P, sd, I, J0, Seff, ws, lane, nt,
+                                      [&](int s2, int r) { return hmax2(acc[s2][r]); });
+            return tdone;
+        }
 #pragma unroll
         for (int s2 = 0; s2 < S; ++s2) {
             if (s2 >= Seff) continue;
