@@ -14,7 +14,8 @@
     - the plain kernel's table equals the two-vector kernel's.
 * The split task queues (tile-only CTAs), with and without column mode,
   forced on at sizes the oracle finishes quickly, so those paths are
-  compared element by element too.
+  compared element by element too; and every work split run repeatedly on
+  the same inputs, tables against the oracle each time.
 """
 import numpy as np
 import pytest
@@ -207,3 +208,24 @@ def test_config3_n32768_structured_sampled():
         assert f.score(seq) == int(D[0, -1])
     finally:
         f.close()
+
+
+def test_layouts_full_tables_repeated():
+    # every work split (automatic, which is column mode at this size, one shared queue, tile-only
+    # CTAs), each fold run twice: the tables must equal the oracle's every time.  The chunks'
+    # merges are bulk reductions whose ordering against the chunk counters rests on async-proxy
+    # fences; a missing fence would show as an occasional stale partial maximum.
+    for seed in range(4):
+        s = synth.variant(["uniform", "gc_rich", "structured"][seed % 3], 2500, 4000 + seed)
+        ref = oracle.nussinov(s)
+        for near, cols in ((-1, -1), (0, -1), (24, 0)):
+            f = fold.Folder(q=8)
+            try:
+                f.option(fold.FOLD_OPT_NEAR_CTAS, near)
+                f.option(fold.FOLD_OPT_COLUMNS, cols)
+                for _ in range(2):
+                    mp, D = f.score(s, want_D=True)
+                    assert mp == ref[0, -1]
+                    assert np.array_equal(D.astype(np.int32), ref)
+            finally:
+                f.close()
