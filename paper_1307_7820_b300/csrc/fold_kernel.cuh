@@ -160,8 +160,10 @@ static __device__ __forceinline__ void red_max(int *p, int v) {
 
 // Bulk reduction of a 16-byte-aligned shared buffer into global memory by the async proxy (one
 // instruction instead of one red per element); the shared source must be made visible to the async
-// proxy first (fence_proxy_async_smem by every writing thread), and the async proxy's global writes
-// must be fenced into the generic proxy (fence_proxy_async_global) before a release publishes them.
+// proxy first (fence_proxy_async_smem by every writing thread), the destination's earlier generic
+// writes that the issuing thread has acquired are ordered before it by fence_proxy_async_global,
+// and the async proxy's global writes are fenced into the generic proxy (fence_proxy_async_global
+// again, after completion) before a release publishes them.
 static __device__ __forceinline__ void bulk_red_max_s32(int *gdst, const int *ssrc, unsigned bytes) {
     asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.max.s32 [%0], [%1], %2;"
                  ::"l"(gdst), "r"((unsigned)__cvta_generic_to_shared(ssrc)), "r"(bytes) : "memory");
@@ -573,6 +575,9 @@ __device__ __forceinline__ long long run_far(const FoldParams &P, const SeqDesc 
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
+            // the slot's zeroing by the tile that used it before (acquired with the input flags, by
+            // the generic proxy) is ordered before the async proxy's reduction into it
+            fence_proxy_async_global();
             bulk_red_max_s32(slot, ws.pbuf, (unsigned)(T * T * sizeof(int)));
             bulk_commit();
         }
@@ -755,6 +760,9 @@ __device__ __forceinline__ void merge_strip_bulk(const FoldParams &P, const SeqD
         __syncwarp();
         if (lane == 0) {
             int *slot = P.pring + sd.p_off + ((size_t)((J0 + s2 - I) % kRing) * NT + I) * (T * T);
+            // the slot's earlier zeroing (generic proxy, acquired with the input flags) before the
+            // async proxy's reduction into it
+            if (s2 == 0) fence_proxy_async_global();
             bulk_red_max_s32(slot, ws.pbuf, (unsigned)(T * T * sizeof(int)));
             bulk_commit();
         }
