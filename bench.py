@@ -13,7 +13,7 @@ A step is one complete fold (every cell of the table).  With --gpus N > 1
 workload (a single fold does not shard); value = all ranks' cells / max time.
 
 --impl reference times the CPU oracle (the plain cubic recurrence) on the
-host cores instead, on a bounded prefix of the same input per step.
+host cores instead: every timed step folds the whole input once.
 """
 from __future__ import annotations
 
@@ -69,6 +69,14 @@ def measured_traffic(n: int, q: int):
         return None
 
 
+def hbm_peak_gbs() -> float:
+    """Measured HBM copy bandwidth of the B300s (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6400.0
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -83,9 +91,12 @@ def parse_args():
     ap.add_argument("--no-qsweep", action="store_true")
     ap.add_argument("--no-sliding", action="store_true", help="skip Section 4's per-column organisation")
     ap.add_argument("--trace", default="", help="write a per-task trace of one fold to this .npy file")
-    ap.add_argument("--serve-rates", default="50,200,1000,2000",
-                    help="Poisson arrival rates (req/s) for the serving run; the workload lists 50-2000")
-    ap.add_argument("--serve-seconds", type=float, default=1.5, help="arrival window per rate")
+    ap.add_argument("--no-sizes", action="store_true", help="skip the single-fold size sweep")
+    ap.add_argument("--serve-rates", default="50,100,200,500,1000,2000",
+                    help="Poisson arrival rates (req/s) for the serving run")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="arrival window per rate (cut to --serve-requests requests at high rates)")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="requests per rate at most")
     return ap.parse_args()
 
 
@@ -157,61 +168,89 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU side
-def cpu_oracle_sample(seq: str, prefix: int):
-    """Time the CPU oracle on seq[:prefix]; project to the full fold by n^3."""
-    import oracle
-    oracle.build()
-    s = seq[:prefix]
-    t0 = time.perf_counter()
-    oracle.score(s)
-    dt = time.perf_counter() - t0
-    n = len(seq)
-    scale = (n / prefix) ** 3 if prefix < n else 1.0
-    full_s = dt * scale
-    return full_s, dt
+# The paper's own figures (Section 6), with the hardware it states: context only.
+PAPER_FIGURES = {
+    "gpu_tesla_c2070_s_at_6000": 2.50,
+    "gpu_geforce_gtx550ti_s_at_6000": 4.97,
+    "serial_two_vector_desktop_s_at_6150": round(1027.8 / 18.1, 1),
+    "serial_nussinov_desktop_s_at_6150": 1027.8,
+    "serial_two_vector_server_s_at_6000": 15,
+    "desktop": "Pentium II 3 GHz, 1 MB cache (as the paper states); the server is not described",
+    "note": "the paper's times on its own hardware; not this metric on this workload",
+}
 
 
-def cpu_two_vector_sample(seq: str, prefix: int, q: int):
-    """Time the oracle's CPU two-vector (Algorithm 1) on seq[:prefix]; project by n^3."""
+def host_info():
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count()
+    return {"cpu_model": model, "cpu_count": os.cpu_count(), "cpus_usable": usable}
+
+
+def cpu_oracle_fold(seq: str):
+    """Seconds of one whole fold of seq by the CPU oracle (single-threaded C, Eq. 1), and its answer."""
     import oracle
     oracle.build()
-    s = seq[:prefix]
     t0 = time.perf_counter()
-    oracle.two_vector(s, q)
-    dt = time.perf_counter() - t0
-    n = len(seq)
-    scale = (n / prefix) ** 3 if prefix < n else 1.0
-    return dt * scale, dt
+    mp = oracle.score(seq)
+    return time.perf_counter() - t0, mp
+
+
+def cpu_two_vector_fold(seq: str, q: int, threads: int):
+    """Seconds of one whole fold by the multi-threaded CPU two-vector program, answer, threads used."""
+    import baseline
+    baseline.build()
+    t0 = time.perf_counter()
+    mp, _, _, used = baseline.fold(seq, q=q, threads=threads)
+    return time.perf_counter() - t0, mp, used
 
 
 def run_reference(a):
-    """--impl reference: the CPU oracle as it stands, on the host cores."""
+    """--impl reference: the CPU oracle as it stands, on the host cores; every timed step is one
+    whole fold of the workload's input (warm-up steps fold a 1000-base prefix: there is nothing to
+    warm in a CPU program beyond its code and pages)."""
     from paper_1307_7820_b300 import metrics, synth
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     seq = synth.uniform(a.n, 1308)
-    prefix = min(a.n, 3000)
     for _ in range(a.warmup):
-        cpu_oracle_sample(seq, min(prefix, 1000))
-    times = [cpu_oracle_sample(seq, prefix)[0] for _ in range(a.steps)]
+        cpu_oracle_fold(seq[:1000])
+    times = []
+    answers = set()
+    for _ in range(a.steps):
+        dt, mp = cpu_oracle_fold(seq)
+        times.append(dt)
+        answers.add(mp)
+    assert len(answers) == 1
     ms = 1e3 * statistics.mean(times)
     value = metrics.cells(a.n) / (ms * 1e-3)
-    sample = (f"each step folds the first {prefix} bases of the n={a.n} input with the cubic oracle "
-              f"(single-threaded C, Eq. 1) and scales its time by (n/{prefix})^3 to one full fold")
+    sample = (f"every timed step folds the whole n={a.n} input once with the cubic oracle (single-threaded C, "
+              f"Eq. 1); measured, not scaled; warm-up steps fold its first 1000 bases")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic", "config": workload_config(a),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         **host_info()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "max_pairs": answers.pop(), "paper": PAPER_FIGURES,
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
 # ------------------------------------------------------------------ serving
-def serve_bench(f, rates, seconds, dev, stream, torch, fold, metrics, synth):
+def serve_bench(f, rates, seconds, max_requests, dev, stream, torch, fold, metrics, synth):
     """Continuous batching under Poisson arrivals vs folding the same requests one at a time."""
     import threading
     out = []
@@ -225,7 +264,7 @@ def serve_bench(f, rates, seconds, dev, stream, torch, fold, metrics, synth):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     for ri, rate in enumerate(rates):
-        count = max(8, int(rate * seconds))
+        count = max(8, min(int(rate * seconds), max_requests))
         reqs = synth.serve_requests(rate, count, 50, 8000, synth.SEED_BASE + 4 + ri)
         fold.fold_serve_start(f.ctx, budget, 4096)
         submit_t = {}
@@ -289,6 +328,7 @@ def serve_bench(f, rates, seconds, dev, stream, torch, fold, metrics, synth):
                     "one_at_a_time_note": "device time of every request folded alone, back to back",
                     "slices": st["slices"], "solo": st["solo"], "tasks_per_slice": st["tasks"] / max(1, st["slices"]),
                     "gpu_busy": st["gpu_ms"] / (1e3 * wall), "host_prep_ms": st["prep_ms"],
+                    "window_s": float(reqs[-1][0]),
                     "lengths": "log-uniform [50, 8000]; 80% uniform, 10% GC-rich, 10% structured",
                     "budget_bytes": budget, "warm_s": warm_s})
     return out
@@ -377,6 +417,50 @@ def main():
     r_pl = device_run(pl, max(3, a.steps // 4), a.warmup)
     pl_ms = statistics.mean(r_pl["step_ms"])
     assert r_pl["max_pairs"] == r_tv["max_pairs"], "plain and two-vector disagree"
+
+    # ---- single folds by size: two-vector vs plain, device time (best of a few, L2 flushed before
+    # each), cells/s and the lookup-roofline fraction; uniform at every size, GC-rich at 6000
+    sizes = None
+    if not a.no_sizes and rank == 0:
+        sizes = []
+        for kind, nn in (("uniform", 2000), ("uniform", 4000), ("gc_rich", 6000), ("uniform", 8000),
+                         ("uniform", 16384), ("uniform", 32768)):
+            s_seq = synth.variant(kind, nn, 1308)
+            reps = 5 if nn <= 8000 else (3 if nn <= 16384 else 2)
+            row = {"n": nn, "kind": kind, "q": q}
+            answers = {}
+            for method in ("two_vector", "plain"):
+                fm = make(method)
+                codes = torch.from_numpy(fold.encode_codes(s_seq)).to(dev)
+                wsm = torch.empty(fm.workspace_bytes(nn), dtype=torch.uint8, device=dev)
+                outm = torch.zeros(1, dtype=torch.int32, device=dev)
+                ts, ks = [], []
+                for k in range(reps + 1):
+                    with torch.cuda.stream(stream):
+                        flush.zero_()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        fm.score_dev(codes, wsm, outm, None, stream=stream.cuda_stream)
+                        e1.record(stream)
+                    e1.synchronize()
+                    if k > 0:
+                        ts.append(e0.elapsed_time(e1))
+                        ks.append(fm.option(fold.FOLD_OPT_KERNEL_NS) / 1e6)
+                answers[method] = int(outm.item())
+                row[method] = {"ms": min(ts), "kernel_ms": min(ks), "cells_per_s": metrics.cells(nn) / (min(ts) * 1e-3)}
+                fm.close()
+                del wsm
+            assert answers["two_vector"] == answers["plain"], f"n={nn}: kernels disagree"
+            lam_n = metrics.lookups(nn, q)
+            row["max_pairs"] = answers["two_vector"]
+            row["two_vector_speedup"] = row["plain"]["ms"] / row["two_vector"]["ms"]
+            row["lookups"] = lam_n
+            row["lookup_frac"] = lam_n / (row["two_vector"]["kernel_ms"] * 1e-3) / metrics.lookup_peak(n_sm, 2032.0)
+            row["plain_dpx_frac"] = (metrics.splits(nn) / (row["plain"]["kernel_ms"] * 1e-3)
+                                     / (n_sm * 128 * 2032e6))
+            sizes.append(row)
+        torch.cuda.empty_cache()
 
     # ---- Section 3.2's partially memoised variant: R rows tabulated on first sight in each CTA
     memo = None
@@ -521,8 +605,8 @@ def main():
     # ---- serving: Poisson arrivals, lengths log-uniform in [50, 8000], 60 GB D budget
     serve = None
     if not a.no_serve:
-        serve = serve_bench(tv, [float(x) for x in a.serve_rates.split(",") if x], a.serve_seconds, dev, stream,
-                            torch, fold, metrics, synth)
+        serve = serve_bench(tv, [float(x) for x in a.serve_rates.split(",") if x], a.serve_seconds,
+                            a.serve_requests, dev, stream, torch, fold, metrics, synth)
 
     # ---- q sweep of the same fold (device time, best of 3 per q, automatic work split)
     qsweep = None
@@ -551,20 +635,47 @@ def main():
         best = min(qsweep, key=lambda k: qsweep[k]["ms"])
         qsweep["best_q"] = int(best)
 
-    # ---- CPU baselines on bounded samples (rank 0, N = 1 only)
+    # ---- CPU baselines, whole folds of the same input, measured (rank 0, N = 1 only)
     cpu = None
     cpu_tv = None
+    cpu_tv_mt = None
     if not a.no_cpu and rank == 0 and world == 1:
-        prefix = min(n, 4000)
-        full_s, dt = cpu_oracle_sample(seq, prefix)
-        cpu = {"value": cells / full_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"cubic oracle (single-threaded C, Eq. 1) on the first {prefix} of the {n} bases took "
-                         f"{dt:.2f} s; time scaled by ({n}/{prefix})^3 to one full fold ({full_s:.1f} s)"}
-        prefix2 = min(n, 3000)
-        full2, dt2 = cpu_two_vector_sample(seq, prefix2, q)
-        cpu_tv = {"value": cells / full2, "unit": UNIT, "cores": 1, "kind": "oracle two-vector (Algorithm 1)",
-                  "sample": f"single-threaded C Algorithm 1, q={q}, on the first {prefix2} bases took {dt2:.2f} s; "
-                            f"scaled by ({n}/{prefix2})^3 to one full fold ({full2:.1f} s)"}
+        hinfo = host_info()
+        dt, mp = cpu_oracle_fold(seq)
+        assert mp == r_tv["max_pairs"], "CPU oracle and GPU disagree"
+        cpu = {"value": cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one whole fold of the n={n} input by the cubic oracle (single-threaded C, Eq. 1): "
+                         f"{dt:.1f} s, measured", **hinfo}
+        dt1, mp1, _ = cpu_two_vector_fold(seq, q, 1)
+        assert mp1 == r_tv["max_pairs"]
+        cpu_tv = {"value": cells / dt1, "unit": UNIT, "cores": 1, "q": q,
+                  "kind": "CPU two-vector (Algorithm 1, tiled wavefront; independent C program)",
+                  "seconds": dt1, "sample": f"one whole fold of the n={n} input on 1 thread, measured"}
+        per_q = {}
+        used = 1
+        for qq in range(4, 11):
+            dq, mq, used = cpu_two_vector_fold(seq, qq, 0)
+            assert mq == r_tv["max_pairs"]
+            per_q[str(qq)] = {"seconds": dq, "cells_per_s": cells / dq}
+        best_q = min(per_q, key=lambda k: per_q[k]["seconds"])
+        cpu_tv_mt = {"value": per_q[str(q)]["cells_per_s"], "unit": UNIT, "cores": used, "q": q,
+                     "seconds": per_q[str(q)]["seconds"], "best_q": int(best_q),
+                     "best_q_value": per_q[best_q]["cells_per_s"], "best_q_seconds": per_q[best_q]["seconds"],
+                     "per_q": per_q, "kind": "CPU two-vector (Algorithm 1, OpenMP over tile anti-diagonals)",
+                     "sample": f"one whole fold of the n={n} input per q on all {used} host threads, measured",
+                     **hinfo}
+
+    # ---- attainable shared-memory lookup rate (microbenchmark; lookups per SM clock per SM)
+    lookup_rates = None
+    if rank == 0:
+        lookup_rates = {}
+        for mode, name in ((0, "uniform_row_registers"), (1, "uniform_row_kernel_step"), (2, "random_row")):
+            r, kms = fold.fold_lookup_rate(local, 8, mode, 4096)
+            lookup_rates[name] = r
+        lookup_rates["analytic"] = 32.0
+        lookup_rates["note"] = ("R-sized (q = 8, 16 KiB) byte table in shared memory, every SM full of resident "
+                                "warps, cycles from clock64: uniform row = one row of R per warp-wide lookup "
+                                "(the fold kernel's pattern); random row = independent (h, c) per lane")
 
     clocks = r_tv["clocks"] or {}
     sm_mhz = clocks.get("sm_mhz") or 2032.0
@@ -578,8 +689,18 @@ def main():
         "algorithmic_lookups": lam,
         "peak_basis": f"{n_sm} SMs x 32 conflict-free shared-memory lookups/clk x 2032 MHz max SM clock",
         "frac_at_sampled_clock": achieved / metrics.lookup_peak(n_sm, sm_mhz),
-        "hbm_floor_ms": metrics.hbm_bytes(n) / 6479.6e9 * 1e3,
+        "hbm_floor_ms": metrics.hbm_bytes(n) / hbm_peak_gbs() / 1e6,
+        "hbm_floor_basis": (f"8 B/cell (two int16 copies written and read once) at {hbm_peak_gbs():.1f} GB/s "
+                            f"measured copy bandwidth; the two-vector kernel in column mode writes one row-major "
+                            f"int16 copy plus packed (D << 16 | bits) row and column features instead of the "
+                            f"column-major copy, so its compulsory bytes are 2 B/cell + 8 B per q cells"),
     }
+    if lookup_rates:
+        per_clk = achieved / (n_sm * 2032e6)
+        roofline["lookups_per_clk_sm"] = per_clk
+        roofline["measured_ceiling_lookups_per_clk_sm"] = lookup_rates["uniform_row_registers"]
+        roofline["frac_of_measured_ceiling"] = per_clk / lookup_rates["uniform_row_registers"]
+        roofline["frac_of_kernel_step_rate"] = per_clk / lookup_rates["uniform_row_kernel_step"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -592,7 +713,9 @@ def main():
         "memoized": memo,
         "sliding": sliding,
         "fg": fgr,
-        "batch": batch, "serve": serve, "q_sweep": qsweep, "cpu_two_vector": cpu_tv, "structure": structure,
+        "sizes": sizes, "lookup_rates": lookup_rates,
+        "batch": batch, "serve": serve, "q_sweep": qsweep, "cpu_two_vector": cpu_tv,
+        "cpu_two_vector_mt": cpu_tv_mt, "paper": PAPER_FIGURES, "structure": structure,
         "max_pairs": r_tv["max_pairs"],
     }
     if rank == 0:

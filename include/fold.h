@@ -140,6 +140,16 @@ void fold_destroy(fold_ctx *ctx);
 /* Static, human-readable text for a status code. */
 const char *fold_strerror(int code);
 
+/* Section 2's alphabet as the device entry points take it: writes the code of
+ * seq[k] (A=0, C=1, G=2, U=3, either case) to codes_out[k] for k < n.  Both
+ * buffers are host memory owned by the caller; codes_out needs n bytes.
+ * FOLD_EINVAL if a letter is not one of ACGUacgu (codes_out is then partly
+ * written), n is outside [0, FOLD_MAX_N] or a pointer is NULL with n > 0.
+ * fold_score, fold_batch and fold_serve_submit apply the same mapping
+ * themselves; callers of fold_score_dev, fold_structure_dev and
+ * fold_score_static encode with this before copying the codes to the device. */
+int fold_encode(const char *seq, int32_t n, uint8_t *codes_out);
+
 /* Sets / reads an option (enum fold_option).  FOLD_EINVAL on an unknown
  * option or out-of-range value. */
 int fold_set_option(fold_ctx *ctx, int option, int64_t value);
@@ -290,13 +300,33 @@ int fold_tune_load(fold_ctx *ctx, const char *path);
  *               enqueued there and returns without waiting.
  * Two-vector method with q = 8 on the current device.  It allocates no device
  * memory (no cudaMalloc, cudaFree or allocating library call).  All calls
- * share the one scratch array, so calls that overlap on the GPU (different
- * streams or threads) race and corrupt each other: serialise them.  The first
- * call on a device does that device's set-up (finds the array's device
- * address, builds the R table, synchronises the stream); make it before any
- * stream capture. */
+ * share the one scratch array, which keeps the last call's contents (each
+ * call clears what must start at zero), so calls that overlap on the GPU
+ * (different streams or threads) race and corrupt each other: serialise
+ * them.  The first call on a device does that device's set-up: it finds the
+ * array's device address, builds the R table, copies the task lists of every
+ * tile count up to FOLD_STATIC_MAX_N from host memory into the array and
+ * synchronises the stream; make that first call before any stream capture.
+ * Every later call does host arithmetic and enqueues one memset and a few
+ * kernel launches, with no host-to-device copy (the sequence descriptor is
+ * passed as a kernel argument).  The set-up is not redone after
+ * cudaDeviceReset: do not use this entry point on a device after resetting it
+ * in the same process. */
 int fold_score_static(const uint8_t *d_codes, int32_t n, uint16_t pair_mask, int32_t *d_max_pairs,
                       int16_t *d_D_out, void *stream);
+
+/* Measures the attainable rate of R-table lookups in shared memory (Section
+ * 3.1, Eq. 3: a byte load at index (h << (q-1)) | c, an add and a max) with a
+ * full GPU of resident warps on `device`.  mode 0: warp-uniform row h, lane
+ * column c, indices in registers (the table-lookup pattern alone); mode 1:
+ * the fold kernel's inner step (row-feature words staged in shared memory,
+ * four per 16-byte broadcast load, the lane's column feature in a register);
+ * mode 2: independent random (h, c) per lane (bank conflicts).  q in [2, 9]
+ * (mode 0: [6, 9]); iters in [1, 2^20] steps of 32 lookups per thread.
+ * Writes lookups per SM clock per SM (from each CTA's clock64 cycles) and,
+ * if kernel_ms is not NULL, the timed launch's duration.  Allocates a few
+ * bytes of device memory per call.  FOLD_EINVAL on bad arguments. */
+int fold_lookup_rate(int device, int q, int mode, int32_t iters, double *lookups_per_clk_sm, double *kernel_ms);
 
 /* Serving (continuous batching).  fold_serve_start starts a host scheduler
  * thread that admits submitted requests while the device memory their two

@@ -615,6 +615,11 @@ const char *fold_strerror(int code) {
     return "unknown status";
 }
 
+int fold_encode(const char *seq, int32_t n, uint8_t *codes_out) {
+    if (n < 0 || n > FOLD_MAX_N || (n > 0 && (!seq || !codes_out))) return FOLD_EINVAL;
+    return encode_seq(seq, n, codes_out) ? FOLD_OK : FOLD_EINVAL;
+}
+
 int fold_init(int q, uint16_t pair_mask, int device, fold_ctx **out) {
     if (!out) return FOLD_EINVAL;
     *out = nullptr;

@@ -29,13 +29,13 @@ FOLD_STATIC_MAX_N = 1024
 
 #: every symbol include/fold.h declares
 ABI_SYMBOLS = (
-    "fold_init", "fold_destroy", "fold_strerror", "fold_set_option", "fold_get_option", "fold_rtable",
+    "fold_init", "fold_destroy", "fold_strerror", "fold_encode", "fold_set_option", "fold_get_option", "fold_rtable",
     "fold_score", "fold_workspace_bytes", "fold_score_dev", "fold_batch",
     "fold_serve_start", "fold_serve_submit", "fold_serve_poll", "fold_serve_stop", "fold_serve_stats_get",
     "fold_serve_warm", "fold_serve_wait_any",
     "fold_trace_copy",
     "fold_score_static", "fold_schedule_check", "fold_batch_schedule_check", "fold_tune", "fold_tune_q", "fold_tune_save", "fold_tune_load",
-    "fold_structure", "fold_structure_workspace_bytes", "fold_structure_dev",
+    "fold_structure", "fold_structure_workspace_bytes", "fold_structure_dev", "fold_lookup_rate",
 )
 
 
@@ -113,6 +113,10 @@ def lib():
     L.fold_serve_wait_any.restype = ctypes.c_int
     L.fold_trace_copy.argtypes = [vp, vp, i64]
     L.fold_score_static.argtypes = [vp, i32, u16, vp, vp, vp]
+    L.fold_encode.argtypes = [ctypes.c_char_p, i32, vp]
+    L.fold_lookup_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i32, P(ctypes.c_double), P(ctypes.c_double)]
+    L.fold_lookup_rate.restype = ctypes.c_int
+    L.fold_encode.restype = ctypes.c_int
     L.fold_score_static.restype = ctypes.c_int
     L.fold_schedule_check.argtypes = [i32, ctypes.c_int, ctypes.c_int, i32]
     L.fold_schedule_check.restype = ctypes.c_int
@@ -237,6 +241,14 @@ def fold_score_static(d_codes: int | None, n: int, pair_mask: int, d_max_pairs: 
                       d_D_out: int | None = None, stream: int | None = None) -> None:
     """Allocation-free fold of up to FOLD_STATIC_MAX_N bases (device pointers as ints)."""
     _check(lib().fold_score_static(d_codes, n, pair_mask, d_max_pairs, d_D_out, stream), "fold_score_static")
+
+
+def fold_lookup_rate(device: int = 0, q: int = 8, mode: int = 0, iters: int = 4096):
+    """(lookups per SM clock per SM, kernel ms) of the shared-memory R-lookup microbenchmark."""
+    r = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    _check(lib().fold_lookup_rate(device, q, mode, iters, ctypes.byref(r), ctypes.byref(ms)), "fold_lookup_rate")
+    return r.value, ms.value
 
 
 def fold_batch_schedule_check(lens, q: int = 8, method: int = FOLD_METHOD_TWO_VECTOR, kchunk: int = 0) -> int:
@@ -423,12 +435,9 @@ class Folder:
 
 
 def encode_codes(seq: str) -> np.ndarray:
-    """Base letters to codes 0..3 (for the device path); raises on other letters."""
-    b = np.frombuffer(seq.encode("ascii"), dtype=np.uint8)
-    lut = np.full(256, 255, dtype=np.uint8)
-    for ch, v in zip(b"ACGUacgu", (0, 1, 2, 3, 0, 1, 2, 3)):
-        lut[ch] = v
-    c = lut[b]
-    if c.size and c.max() == 255:
-        raise ValueError("invalid base letter")
-    return c
+    """Base letters to codes 0..3 for the device entry points, by the library's fold_encode
+    (raises FoldError with FOLD_EINVAL on other letters)."""
+    raw = seq.encode("ascii", errors="replace")
+    out = np.empty(len(raw), dtype=np.uint8)
+    _check(lib().fold_encode(raw, len(raw), out.ctypes.data if len(raw) else None), "fold_encode")
+    return out

@@ -69,3 +69,19 @@ def test_pair_mask_constants():
     import oracle
     assert fold.FOLD_PAIRS_DEFAULT == oracle.MASK6
     assert fold.FOLD_PAIRS_PAPER == oracle.MASK4
+
+
+def test_encode_is_the_section2_alphabet(L):
+    """fold_encode (host only) maps A, C, G, U in either case to 0..3 and rejects anything else."""
+    import numpy as np
+    c = fold.encode_codes("ACGUacguGGGAAAUCC")
+    assert c.tolist() == [0, 1, 2, 3, 0, 1, 2, 3, 2, 2, 2, 0, 0, 0, 3, 1, 1]
+    assert fold.encode_codes("").size == 0
+    for bad in ["ACGT", "AC GU", "N", "acgu\x00", "ACGU\u00e9"]:
+        with pytest.raises(fold.FoldError) as ei:
+            fold.encode_codes(bad)
+        assert ei.value.code == fold.FOLD_EINVAL
+    out = np.zeros(4, dtype=np.uint8)
+    assert L.fold_encode(None, 4, out.ctypes.data) == fold.FOLD_EINVAL
+    assert L.fold_encode(b"ACGU", -1, out.ctypes.data) == fold.FOLD_EINVAL
+    assert L.fold_encode(b"ACGU", 4, None) == fold.FOLD_EINVAL

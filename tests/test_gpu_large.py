@@ -2,89 +2,54 @@
 
 * Single folds of n = 4000 and 6000 (uniform and GC-rich, q swept 4..10):
   the whole D table against the CPU oracle (Eq. 1), element by element.
-* Large folds, n = 8000, 16384 and 32768 (uniform and the structured
-  segment + reverse-complement variant), where the cubic oracle takes too
-  long for the whole table:
-    - sampled cells against the oracle: D(i,j) depends only on s_i..s_j, so
-      the oracle's score of that substring is the expected value;
-    - the unit-step invariants of Lemma 1 over the whole table
-      (0 <= D(i,j+1) - D(i,j) <= 1 and 0 <= D(i-1,j) - D(i,j) <= 1);
-    - Eq. 1 re-evaluated from the returned table at sampled cells, including
-      the answer cell (0, n-1);
-    - the plain kernel's table equals the two-vector kernel's.
+* Large folds, n = 8000, 16384 and 32768 (uniform, GC-rich and the
+  structured segment + reverse-complement variant): the whole table against
+  the CPU oracle's, through digests the oracle wrote once
+  (oracle/make_digests.py, stored in tests/golden/digest_*.txt): the SHA-256
+  of the row-major int16 table, the CRC-32 of every row and D(0, n-1).  A
+  mismatch names the rows that differ.
 * The split task queues (tile-only CTAs), with and without column mode,
   forced on at sizes the oracle finishes quickly, so those paths are
   compared element by element too; and every work split run repeatedly on
   the same inputs, tables against the oracle each time.
 """
+import hashlib
+
 import numpy as np
 import pytest
 
 import oracle
+from oracle.make_digests import digest_path, read_digest, table_digests
 from paper_1307_7820_b300 import fold, synth
 
 pytestmark = pytest.mark.gpu
-
-BASE = {"A": 0, "C": 1, "G": 2, "U": 3}
-
 
 def _full_equal(D, ref):
     bad = np.argwhere(D.astype(np.int32) != ref)
     assert bad.size == 0, f"first mismatch at {bad[0].tolist()}: gpu={D[tuple(bad[0])]} ref={ref[tuple(bad[0])]}"
 
 
-def _check_invariants(D, block=4096):
-    """Lemma 1 over the whole table (lower triangle and diagonal are zero)."""
-    n = D.shape[0]
-    assert not np.any(np.diagonal(D))
-    for r0 in range(0, n, block):
-        r1 = min(n, r0 + block)
-        rows = D[r0:r1]
-        assert not np.any(np.tril(rows, r0 - 1)), "nonzero entry below the diagonal"
-        dh = np.diff(rows, axis=1)
-        assert dh.min() >= 0 and dh.max() <= 1, f"row step outside {{0,1}} in rows {r0}..{r1}"
-        if r0 > 0:
-            dv = D[r0 - 1:r1 - 1].astype(np.int16) - rows
-            assert dv.min() >= 0 and dv.max() <= 1, f"column step outside {{0,1}} in rows {r0}..{r1}"
-        else:
-            dv = rows[:-1] - rows[1:]
-            assert dv.min() >= 0 and dv.max() <= 1
-
-
-def _eq1_at(D, codes, mask, i, j):
-    """Eq. 1 evaluated at (i, j) from the returned table itself."""
-    inner = int(D[i + 1, j - 1]) if i + 1 <= j - 1 else 0
-    best = ((mask >> (4 * int(codes[i]) + int(codes[j]))) & 1) + inner
-    split = D[i, i:j].astype(np.int32) + D[i + 1:j + 1, j].astype(np.int32)
-    return max(best, int(split.max()))
-
-
-def _sample_cells(n, count, max_span, rng):
-    cells = []
-    for _ in range(count):
-        span = int(rng.integers(1, max_span))
-        i = int(rng.integers(0, n - span))
-        cells.append((i, i + span))
-    return cells
-
-
-def _large_checks(f, seq, mask, rng, D_other=None):
+def _digest_check(D, seq, variant, seed, what, mask=oracle.MASK6):
+    """The whole table D (n*n int16) against the oracle's digest of the same input."""
     n = len(seq)
-    mp, D = f.score(seq, want_D=True)
-    assert mp == int(D[0, n - 1])
-    _check_invariants(D)
-    codes = np.array([BASE[c] for c in seq], dtype=np.int64)
-    # Eq. 1 at sampled cells of every span, the answer cell and the last row/column
-    picks = [(0, n - 1), (0, n // 2), (n // 2, n - 1), (n - 2, n - 1)]
-    picks += [(int(a), int(a) + int(b)) for a, b in zip(rng.integers(0, n // 2, 200), rng.integers(1, n // 2, 200))]
-    for i, j in picks:
-        assert int(D[i, j]) == _eq1_at(D, codes, mask, i, j), f"Eq. 1 fails at ({i},{j})"
-    # short spans against the oracle on the substring
-    for i, j in _sample_cells(n, 40, 500, rng):
-        assert int(D[i, j]) == oracle.score(seq[i:j + 1], mask), f"cell ({i},{j})"
-    if D_other is not None:
-        assert np.array_equal(D, D_other)
-    return D
+    ref = read_digest(digest_path(n, variant, mask))
+    assert (ref["n"], ref["variant"], ref["seed"], ref["mask"]) == (n, variant, seed, mask)
+    assert ref["seq_sha256"] == hashlib.sha256(seq.encode()).hexdigest(), "the input generator changed"
+    assert int(D[0, n - 1]) == ref["score"], f"{what}: D(0,n-1) = {int(D[0, n - 1])}, oracle {ref['score']}"
+    sha, crcs = table_digests(D)
+    if sha != ref["table_sha256"]:
+        bad = [i for i, (x, y) in enumerate(zip(crcs, ref["row_crc32"])) if x != y]
+        pytest.fail(f"{what}: table differs from the oracle's in {len(bad)} rows, first {bad[:8]}")
+
+
+def _fold_table(method, q, seq):
+    f = fold.Folder(q=q, method=method)
+    try:
+        mp, D = f.score(seq, want_D=True)
+        assert mp == int(D[0, len(seq) - 1])
+        return D
+    finally:
+        f.close()
 
 
 # (n, tile CTAs, column mode): 700 bases are 22 tile columns, 2000 bases 63 (q = 8), so one tile
@@ -164,50 +129,35 @@ def test_config2_n6000_full_table():
 
 @pytest.mark.slow
 @pytest.mark.parametrize("kind", ["uniform", "gc_rich"])
-def test_config2_n8000_sampled(kind):
+def test_config2_n8000_full_table(kind):
     seq = synth.variant(kind, 8000, 8000)
-    rng = np.random.default_rng(8000)
-    fp = fold.Folder(q=8, method="plain")
-    try:
-        Dp = fp.score(seq, want_D=True)[1]
-    finally:
-        fp.close()
+    _digest_check(_fold_table("plain", 8, seq), seq, kind, 8000, "plain")
     for q in [4, 8, 10]:
-        f = fold.Folder(q=q)
-        try:
-            _large_checks(f, seq, oracle.MASK6, rng, D_other=Dp)
-        finally:
-            f.close()
+        _digest_check(_fold_table("two_vector", q, seq), seq, kind, 8000, f"two-vector q={q}")
 
 
 @pytest.mark.slow
 @pytest.mark.parametrize("kind", ["uniform", "structured"])
-def test_config3_n16384_sampled(kind):
+def test_config3_n16384_full_table(kind):
     seq = synth.variant(kind, 16384, 16384)
-    rng = np.random.default_rng(16384)
-    fp = fold.Folder(q=8, method="plain")
-    try:
-        Dp = fp.score(seq, want_D=True)[1]
-    finally:
-        fp.close()
-    f = fold.Folder(q=8)
-    try:
-        _large_checks(f, seq, oracle.MASK6, rng, D_other=Dp)
-    finally:
-        f.close()
+    _digest_check(_fold_table("plain", 8, seq), seq, kind, 16384, "plain")
+    _digest_check(_fold_table("two_vector", 8, seq), seq, kind, 16384, "two-vector q=8")
 
 
 @pytest.mark.slow
-def test_config3_n32768_structured_sampled():
-    seq = synth.structured(32768, 32768)
-    rng = np.random.default_rng(32768)
+@pytest.mark.parametrize("kind", ["structured", "uniform"])
+def test_config3_n32768_full_table(kind):
+    seq = synth.variant(kind, 32768, 32768)
     f = fold.Folder(q=8)
     try:
-        D = _large_checks(f, seq, oracle.MASK6, rng)
+        mp, D = f.score(seq, want_D=True)
+        _digest_check(D, seq, kind, 32768, "two-vector q=8")
         # the score alone (no table copy) agrees with the table
-        assert f.score(seq) == int(D[0, -1])
+        assert f.score(seq) == mp == int(D[0, -1])
     finally:
         f.close()
+    del D
+    _digest_check(_fold_table("plain", 8, seq), seq, kind, 32768, "plain")
 
 
 def test_layouts_full_tables_repeated():
