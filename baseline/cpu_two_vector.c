@@ -172,8 +172,8 @@ int cpu_two_vector(const uint8_t *codes, int n, int q, uint16_t mask, int thread
     const int NT = (n + st.B - 1) / st.B;
     int64_t nl = 0;
 #ifdef _OPENMP
-    if (threads > 0) omp_set_num_threads(threads);
-#pragma omp parallel reduction(+ : nl)
+    const int nth = threads > 0 ? threads : omp_get_num_procs();
+#pragma omp parallel num_threads(nth) reduction(+ : nl)
     {
 #pragma omp single
         if (threads_used) *threads_used = omp_get_num_threads();

@@ -35,7 +35,7 @@ constexpr int kLbUnroll = 32;
 
 template <int MODE>
 __global__ void __launch_bounds__(kLbThreads) lookup_bench_kernel(int q, int iters, long long *cycles,
-                                                                 int *sink) {
+                                                                 int *sink, int never) {
     extern __shared__ __align__(16) uint8_t lb_smem[];
     const int rbytes = 1 << (2 * (q - 1));
     const int cols = 1 << (q - 1);
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kLbThreads) lookup_bench_kernel(int q, int ite
     }
     long long t1 = clock64();
     if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
-    if (acc == 0x7fffffff) sink[0] = acc;   // keeps the loop; never true
+    if (acc == never) sink[0] = acc;   // `never` is negative at run time: keeps the loop, never stores
 }
 
 }  // namespace
@@ -112,7 +112,7 @@ extern "C" int fold_lookup_rate(int device, int q, int mode, int32_t iters, doub
     }
     if (cudaSetDevice(device) != cudaSuccess) return FOLD_ECUDA;
     const size_t smem = ((size_t)1 << (2 * (q - 1))) + 256;
-    void (*kern)(int, int, long long *, int *) =
+    void (*kern)(int, int, long long *, int *, int) =
         mode == 0 ? lookup_bench_kernel<0> : (mode == 1 ? lookup_bench_kernel<1> : lookup_bench_kernel<2>);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return FOLD_ECUDA;
@@ -131,9 +131,9 @@ extern "C" int fold_lookup_rate(int device, int q, int mode, int32_t iters, doub
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    kern<<<grid, kLbThreads, smem>>>(q, iters / 8 + 1, d_cycles, d_sink);   // warm-up
+    kern<<<grid, kLbThreads, smem>>>(q, iters / 8 + 1, d_cycles, d_sink, -1);   // warm-up
     cudaEventRecord(e0);
-    kern<<<grid, kLbThreads, smem>>>(q, iters, d_cycles, d_sink);
+    kern<<<grid, kLbThreads, smem>>>(q, iters, d_cycles, d_sink, -1);
     cudaEventRecord(e1);
     cudaError_t e = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -151,6 +151,7 @@ extern "C" int fold_lookup_rate(int device, int q, int mode, int32_t iters, doub
     long long cmax = 1;
     for (int b = 0; b < grid; ++b) cmax = h[b] > cmax ? h[b] : cmax;
     delete[] h;
+    if (cmax < (long long)iters) return FOLD_ECUDA;   // fewer cycles than loop steps: the loop did not run
     const double per_cta = (double)kLbThreads / 32 * 32 * (double)iters * kLbUnroll;   // warps x lanes x lookups
     *lookups_per_clk_sm = per_cta * per_sm / (double)cmax;
     if (kernel_ms) *kernel_ms = ms;
