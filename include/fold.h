@@ -104,10 +104,15 @@ enum fold_option {
                                  column vector the first time one of its warps stages a horizontal
                                  vector h; 0 = the table precomputed at fold_init (default).  Results
                                  are identical; FOLD_EINVAL for q = 10, FOLD_EAGAIN while serving. */
-    FOLD_OPT_BATCH_GATHER = 16 /* fold_batch's task list: 1 = gathered on the device from device copies of
+    FOLD_OPT_BATCH_GATHER = 16, /* fold_batch's task list: 1 = gathered on the device from device copies of
                                  the per-size task templates, kept by the context (up to 1 GiB; only a
                                  segment list is copied per call; default); 0 = built on the host and
                                  copied whole.  Results are identical. */
+    FOLD_OPT_COL_HELPERS = 17  /* single folds in column mode, two-vector: -1 = automatic (on where the
+                                  layout has at most 4 columns per tile CTA), 1 = on, 0 = off.  On, warp
+                                  w + 4 of each tile CTA helps column warp w: it loads each tile's inputs,
+                                  does its late middle blocks' lookups and the chunk merge, and publishes
+                                  each finished tile, so the column warp only computes rows */
 };
 
 /* One record per task of the last traced persistent launch. */

@@ -156,12 +156,19 @@ SplitPlan plan_split(fold_ctx *ctx, const FoldOpts &o, int NT, int grid, bool la
     const int nopt = o.near_opt, copt = o.cols_opt;
     if (nopt == 0 || NT < 2 || grid < 2) return sp;
     auto ceil_div = [](int a, int b) { return (a + b - 1) / b; };
+    // column mode with a helper warp per column: two-vector, at most half the CTA's warps as columns;
+    // automatic up to NT = 150 tiles per side (n ~ 4800 at q = 8), where it measured faster (n = 2000:
+    // 0.53 against 0.61 ms, n = 4000: 1.10-1.15 against 1.19 ms); at n = 6000 the end-range chunks
+    // then arrive after the tile could start and it measured slower (2.0 against 1.84 ms)
+    const bool help_ok = ctx->col_helpers_opt != 0 && fold_col_helpers_supported(ctx->q, ctx->method) &&
+                         (ctx->col_helpers_opt == 1 || NT <= 150);
     auto column = [&](int cpc, int near) -> bool {
         near = std::max(near, ceil_div(NT, cpc));
         if (!layout_ok || near > grid - 1) return false;
         sp.near_ctas = near;
         sp.col_mode = 1;
         sp.cpc = cpc;
+        sp.helpers = (help_ok && cpc <= kWarpsPerCta / 2) ? 1 : 0;
         return true;
     };
     if (nopt > 0) {                            // forced tile CTAs
@@ -186,7 +193,7 @@ SplitPlan plan_split(fold_ctx *ctx, const FoldOpts &o, int NT, int grid, bool la
     // tile-diagonal step of each layout (q = 8, measured on B300; with these figures both kernels
     // picked the fastest layout, or one within 1 %, at every size swept from n = 2000 to 16384)
     const double step_one = 20.0, step_split = 13.0;
-    const double step_col[2] = {9.9, 12.5};
+    const double step_col[2] = {help_ok ? 8.5 : 9.9, 12.5};
     double best = model(step_one, 0);
     const int near_split = std::max(2, std::min(ceil_div(NT, kWarpsPerCta), grid / 6));
     const double split = model(step_split, near_split);
@@ -205,6 +212,7 @@ SplitPlan plan_split(fold_ctx *ctx, const FoldOpts &o, int NT, int grid, bool la
             sp.near_ctas = near;
             sp.col_mode = 1;
             sp.cpc = cands[k];
+            sp.helpers = (help_ok && cands[k] <= kWarpsPerCta / 2) ? 1 : 0;
         }
     }
     return sp;
@@ -578,6 +586,7 @@ int enqueue_single(fold_ctx *ctx, const uint8_t *d_codes, int n, uint8_t *ws, si
             const SplitPlan sp = plan_split(ctx, single_opts(ctx, n), pl.NTs[0], grid_for(ctx), layout_ok);
             p.col_mode = sp.col_mode;
             p.cols_per_cta = sp.cpc;
+            p.col_helpers = sp.helpers;
             p.nnear = nnear;
             p.near_ctas = sp.near_ctas;
         }
@@ -727,6 +736,10 @@ int fold_set_option(fold_ctx *ctx, int option, int64_t value) {
             if (value < -1 || value > kWarpsPerCta) return FOLD_EINVAL;
             ctx->columns_opt = (int)value;
             return FOLD_OK;
+        case FOLD_OPT_COL_HELPERS:
+            if (value < -1 || value > 1) return FOLD_EINVAL;
+            ctx->col_helpers_opt = (int)value;
+            return FOLD_OK;
         case FOLD_OPT_BATCH_FLAT:
             if (value < -1 || value > 1) return FOLD_EINVAL;
             ctx->batch_flat_opt = (int)value;
@@ -759,6 +772,7 @@ int fold_get_option(fold_ctx *ctx, int option, int64_t *value) {
         case FOLD_OPT_TRACE: *value = ctx->trace; return FOLD_OK;
         case FOLD_OPT_NEAR_CTAS: *value = ctx->near_ctas_opt; return FOLD_OK;
         case FOLD_OPT_COLUMNS: *value = ctx->columns_opt; return FOLD_OK;
+        case FOLD_OPT_COL_HELPERS: *value = ctx->col_helpers_opt; return FOLD_OK;
         case FOLD_OPT_BATCH_FLAT: *value = ctx->batch_flat_opt; return FOLD_OK;
         case FOLD_OPT_R_MEMO: *value = ctx->r_memo; return FOLD_OK;
         case FOLD_OPT_BATCH_GATHER: *value = ctx->batch_gather; return FOLD_OK;

@@ -68,6 +68,7 @@ struct fold_ctx {
     int test_drop_task = 0;
     int near_ctas_opt = -1;    // -1 automatic, 0 one shared queue, k > 0 k tile-only CTAs
     int columns_opt = -1;      // -1 automatic, 0 off, v >= 1 column mode with v columns per tile CTA
+    int col_helpers_opt = -1;  // FOLD_OPT_COL_HELPERS: -1 automatic, 0 off, 1 on (column mode, two-vector)
     int batch_flat_opt = -1;   // fold_batch chunks: -1 / 1 kc blocks each, 0 geometric sizes
     int batch_gather = 1;      // FOLD_OPT_BATCH_GATHER: fold_batch's list gathered on the device
     int r_memo = 0;            // FOLD_OPT_R_MEMO: tabulate R rows on first sight (two-vector, q <= 9)
@@ -110,6 +111,7 @@ struct SplitPlan {
     int near_ctas = 0;   // tile-only CTAs (0: one shared queue)
     int col_mode = 0;    // 1: column mode
     int cpc = kWarpsPerCta;   // columns per tile CTA in column mode
+    int helpers = 0;     // 1: column mode with a helper warp per column (cpc <= kWarpsPerCta / 2)
 };
 SplitPlan plan_split(fold_ctx *ctx, const FoldOpts &o, int NT, int grid, bool layout_ok);
 FoldOpts single_opts(const fold_ctx *ctx, int n);

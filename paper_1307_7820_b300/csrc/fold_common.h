@@ -77,6 +77,10 @@ struct FoldParams {
     // tasks[0, nnear) still lists them (diagonal by diagonal) for their chunk counts.
     int col_mode;
     int cols_per_cta;
+    // column mode, two-vector: warp w + kWarpsPerCta/2 of each tile CTA is the helper of column warp w
+    // (cols_per_cta <= kWarpsPerCta/2): it prepares each tile's inputs and publishes each finished
+    // tile, so the column warp only computes rows (see fold_column.cuh)
+    int col_helpers;
     // two-vector, q <= 9: launch the kernel instantiation in which R starts empty in each CTA and a
     // row R[h][*] is tabulated against every column vector the first time a warp of the CTA stages a
     // feature with horizontal vector h (Section 3.2's partially memoised variant); 0: the one that

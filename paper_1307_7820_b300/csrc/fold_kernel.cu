@@ -109,6 +109,22 @@ size_t fold_smem_bytes(int q, int method) {
     return 0;
 }
 
+bool fold_col_helpers_supported(int q, int method) {
+    if (method != kTwoVector) return false;
+    switch (q) {
+        case 2: return col_helpers_fit<2>();
+        case 3: return col_helpers_fit<3>();
+        case 4: return col_helpers_fit<4>();
+        case 5: return col_helpers_fit<5>();
+        case 6: return col_helpers_fit<6>();
+        case 7: return col_helpers_fit<7>();
+        case 8: return col_helpers_fit<8>();
+        case 9: return col_helpers_fit<9>();
+        case 10: return col_helpers_fit<10>();
+    }
+    return false;
+}
+
 int fold_blocks_per_sm(int q, int method) {
     if (method == kPlain) return bps_plain();
     switch (q) {

@@ -1586,6 +1586,12 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     return tfar;
 }
 
+}  // namespace fold
+
+#include "fold_column.cuh"
+
+namespace fold {
+
 // ---------------------------------------------------------------- kernel
 // MEMO: Section 3.2's partially memoised variant (R rows tabulated on first sight in each CTA)
 template <int Q, int M, bool MEMO>
@@ -1610,9 +1616,75 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
         ws.produced = 0;
         ws.consumed = 0;
     }
+    constexpr int kHalf = kWarpsPerCta / 2;
+    constexpr bool kHelp = (M == kTwoVector) && col_helpers_fit<Q>();
+    if constexpr (kHelp) {
+        if (P.col_helpers && warp >= kHalf && lane == 0) {
+            ColHelp<Q> *ha = reinterpret_cast<ColHelp<Q> *>(&ws);
+            ha->mprog = 0;
+            ha->prep_ready = 0;
+            ha->consumed = 0;
+        }
+    }
     __syncthreads();
     const bool split = P.near_ctas > 0;
     const bool far_role = split && (int)blockIdx.x >= P.near_ctas;
+    if constexpr (kHelp) {
+        if (P.col_mode && P.col_helpers && split && !far_role) {
+            // column mode with helpers: warp w < kHalf computes the rows of tile column J, warp
+            // w + kHalf is its helper (fold_column.cuh)
+            const SeqDesc sd = P.seqs[0];
+            const int NT = sd.NT;
+            const int cpc = P.cols_per_cta;
+            const int col_ctas = (NT + cpc - 1) / cpc;
+            const bool main_role = warp < kHalf;
+            const int w = main_role ? warp : warp - kHalf;
+            const int J = (col_ctas - 1 - (int)blockIdx.x) * cpc + w;
+            if ((int)blockIdx.x >= col_ctas || w >= cpc || cpc > kHalf || J >= NT) return;
+            ColHelp<Q> &ha = *reinterpret_cast<ColHelp<Q> *>(&wsb[w + kHalf]);
+            const bool consumer = (w + 1 < cpc) && (J + 1 < NT);
+            if (main_role) {
+                ColMain<Q> cs;
+#pragma unroll
+                for (int mm = 0; mm < 16; ++mm) cs.Wp[mm] = 0u;
+                cs.colT = 0;
+                cs.consumer = consumer;
+                for (int k = 0; k <= J; ++k) {
+                    const int I = J - k;
+                    const int idx = k * NT - k * (k - 1) / 2 + I;
+                    long long t0 = 0, tt[2] = {0, 0};
+                    if (P.trace && lane == 0) t0 = (long long)gtimer();
+                    const int nfar = k >= 1 ? P.tasks[idx].z : 0;
+                    const bool ok = col_main_tile<Q, MEMO>(P, sd, I, J, k, nfar, wsb[w], ha, Rs, lane, cs,
+                                                           P.trace ? tt : nullptr);
+                    if (P.trace && lane == 0 && ok) {
+                        long long *rec = P.trace + (size_t)idx * kTraceWords;
+                        rec[0] = ((long long)(blockIdx.x * kWarpsPerCta + warp) << 32) | (unsigned)idx;
+                        rec[1] = ((long long)kTaskNear << 32) | 0u;
+                        rec[2] = ((long long)I << 32) | (unsigned)J;
+                        rec[3] = t0;
+                        rec[4] = tt[0];
+                        rec[5] = tt[0];
+                        rec[6] = (long long)gtimer();
+                        rec[7] = tt[0];
+                        rec[8] = tt[1];
+                        rec[9] = tt[1];
+                        rec[10] = (long long)smid();
+                    }
+                    if (!ok) break;
+                }
+            } else {
+                ColHelper<Q> hs;
+                hs.have_lcb0 = false;
+                hs.sj = lane < Cfg<Q, M>::T ? (int)P.codes[sd.code_off + J * Cfg<Q, M>::T + lane] : kPadCode;
+                WarpScratch<Q, M> *prodM = w > 0 ? &wsb[w - 1] : nullptr;
+                ColHelp<Q> *prodH = w > 0 ? reinterpret_cast<ColHelp<Q> *>(&wsb[w - 1 + kHalf]) : nullptr;
+                for (int k = 0; k <= J; ++k)
+                    if (!col_help_prep<Q, MEMO>(P, sd, J - k, J, k, wsb[w], ha, prodM, prodH, Rs, lane, hs)) break;
+            }
+            return;
+        }
+    }
     if (P.col_mode && split && !far_role) {
         // column mode: this warp computes the tiles of one column, bottom-up
         const SeqDesc sd = P.seqs[0];

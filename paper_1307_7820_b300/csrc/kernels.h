@@ -9,6 +9,8 @@ namespace fold {
 
 size_t fold_smem_bytes(int q, int method);
 int fold_blocks_per_sm(int q, int method);
+// column mode with a helper warp per column (fold_column.cuh) exists for this q and method
+bool fold_col_helpers_supported(int q, int method);
 cudaError_t launch_finalize(const int *error, const int *results, int count, int32_t *out, cudaStream_t st);
 cudaError_t launch_fold(const FoldParams &p, int q, int method, int grid, cudaStream_t st);
 cudaError_t launch_rtable(int q, uint8_t *canon, uint8_t *packed, cudaStream_t st);

@@ -251,6 +251,7 @@ static void serve_loop(ServeState *S) {
                 if (sp.near_ctas > 0) {
                     p.col_mode = sp.col_mode;
                     p.cols_per_cta = sp.cpc;
+                    p.col_helpers = sp.helpers;
                     p.nnear = nnear;
                     p.near_ctas = sp.near_ctas;
                 }
