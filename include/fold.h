@@ -333,6 +333,46 @@ int fold_score_static(const uint8_t *d_codes, int32_t n, uint16_t pair_mask, int
  * bytes of device memory per call.  FOLD_EINVAL on bad arguments. */
 int fold_lookup_rate(int device, int q, int mode, int32_t iters, double *lookups_per_clk_sm, double *kernel_ms);
 
+/* A batch as one capturable launch.  fold_batch encodes host strings, builds
+ * the task list and waits for the answers on every call; for a fixed set of
+ * lengths fold_batch_plan_create does the host part once (synchronously; call
+ * it before any stream capture): the sequences' workspace layout, the task
+ * list of the one persistent launch (every sequence's Section 4 wavefront,
+ * interleaved step by step as fold_batch does) and each sequence's offset in
+ * the concatenated codes, all kept on the device by the plan.  The plan is
+ * tied to ctx and to its q and method at creation (FOLD_EINVAL otherwise).
+ * count >= 1 sequences; lens[k] in [0, FOLD_MAX_N]; sliding/FG methods:
+ * FOLD_EINVAL.  fold_batch_plan_destroy synchronises the device first, so no
+ * enqueued fold of the plan is still reading its lists. */
+typedef struct fold_batch_plan fold_batch_plan;
+int fold_batch_plan_create(fold_ctx *ctx, int32_t count, const int32_t *lens, fold_batch_plan **out);
+/* Workspace bytes fold_batch_dev needs, and the bytes of its concatenated codes
+ * (the sum of the lengths); negative status on a NULL plan. */
+int64_t fold_batch_plan_workspace_bytes(const fold_batch_plan *plan);
+int64_t fold_batch_plan_codes_bytes(const fold_batch_plan *plan);
+void fold_batch_plan_destroy(fold_batch_plan *plan);
+/* Enqueues the fold of the planned batch on `stream` (cudaStream_t, NULL =
+ * the CUDA default stream) and returns without waiting:
+ *   d_codes     device bytes, codes 0..3 of every sequence back to back:
+ *               sequence k starts at lens[0] + ... + lens[k-1];
+ *   d_ws        device workspace, >= fold_batch_plan_workspace_bytes, 256-byte
+ *               aligned, caller-owned, not reused until the stream has passed
+ *               this call (it also holds the tables, see fold_batch_dev_table);
+ *   d_max_pairs count device int32: D(0, n_k - 1) (0 for n_k <= 1), or
+ *               -FOLD_ETIMEOUT if a device-side wait expired.
+ * It allocates nothing, copies nothing from the host and does not
+ * synchronise: one memset and three kernel launches, which stream capture
+ * records into a CUDA graph whose replays fold whatever d_codes then holds.
+ * FOLD_EINVAL under capture with FOLD_OPT_TIMING or FOLD_OPT_TRACE on, or on a
+ * bad argument; FOLD_ENOMEM if ws_bytes is too small. */
+int fold_batch_dev(fold_ctx *ctx, const fold_batch_plan *plan, const uint8_t *d_codes, void *d_ws, int64_t ws_bytes,
+                   int32_t *d_max_pairs, void *stream);
+/* Enqueues the copy of sequence k's n_k x n_k int16 table (row-major, zero below
+ * the diagonal) from the workspace of a fold_batch_dev call to device memory
+ * d_D_out; nothing for n_k = 0.  Capturable like fold_batch_dev. */
+int fold_batch_dev_table(fold_ctx *ctx, const fold_batch_plan *plan, const void *d_ws, int32_t k, int16_t *d_D_out,
+                         void *stream);
+
 /* Serving (continuous batching).  fold_serve_start starts a host scheduler
  * thread that admits submitted requests while the device memory their two
  * int16 D copies need (about 4*n^2 bytes each) fits `budget_bytes` and at

@@ -37,6 +37,8 @@ ABI_SYMBOLS = (
     "fold_trace_copy",
     "fold_score_static", "fold_schedule_check", "fold_batch_schedule_check", "fold_tune", "fold_tune_q", "fold_tune_save", "fold_tune_load",
     "fold_structure", "fold_structure_workspace_bytes", "fold_structure_dev", "fold_lookup_rate",
+    "fold_batch_plan_create", "fold_batch_plan_workspace_bytes", "fold_batch_plan_codes_bytes",
+    "fold_batch_plan_destroy", "fold_batch_dev", "fold_batch_dev_table",
 )
 
 
@@ -117,6 +119,18 @@ def lib():
     L.fold_encode.argtypes = [ctypes.c_char_p, i32, vp]
     L.fold_lookup_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i32, P(ctypes.c_double), P(ctypes.c_double)]
     L.fold_lookup_rate.restype = ctypes.c_int
+    L.fold_batch_plan_create.argtypes = [vp, i32, P(i32), P(vp)]
+    L.fold_batch_plan_create.restype = ctypes.c_int
+    L.fold_batch_plan_workspace_bytes.argtypes = [vp]
+    L.fold_batch_plan_workspace_bytes.restype = i64
+    L.fold_batch_plan_codes_bytes.argtypes = [vp]
+    L.fold_batch_plan_codes_bytes.restype = i64
+    L.fold_batch_plan_destroy.argtypes = [vp]
+    L.fold_batch_plan_destroy.restype = None
+    L.fold_batch_dev.argtypes = [vp, vp, vp, vp, i64, vp, vp]
+    L.fold_batch_dev.restype = ctypes.c_int
+    L.fold_batch_dev_table.argtypes = [vp, vp, vp, i32, vp, vp]
+    L.fold_batch_dev_table.restype = ctypes.c_int
     L.fold_encode.restype = ctypes.c_int
     L.fold_score_static.restype = ctypes.c_int
     L.fold_schedule_check.argtypes = [i32, ctypes.c_int, ctypes.c_int, i32]
@@ -242,6 +256,44 @@ def fold_score_static(d_codes: int | None, n: int, pair_mask: int, d_max_pairs: 
                       d_D_out: int | None = None, stream: int | None = None) -> None:
     """Allocation-free fold of up to FOLD_STATIC_MAX_N bases (device pointers as ints)."""
     _check(lib().fold_score_static(d_codes, n, pair_mask, d_max_pairs, d_D_out, stream), "fold_score_static")
+
+
+class BatchPlan:
+    """A batch planned once (fold_batch_plan_create) and folded from device buffers by
+    fold_batch_dev, which stream capture can record into a CUDA graph."""
+
+    def __init__(self, ctx: int, lens):
+        self.lens = np.ascontiguousarray(lens, dtype=np.int32)
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        _check(lib().fold_batch_plan_create(ctx, len(self.lens), self.lens.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                            ctypes.byref(h)), "fold_batch_plan_create")
+        self.h = h.value
+        self.offsets = np.concatenate([[0], np.cumsum(self.lens.astype(np.int64))[:-1]]) if len(self.lens) else np.zeros(0)
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(lib().fold_batch_plan_workspace_bytes(self.h))
+
+    @property
+    def codes_bytes(self) -> int:
+        return int(lib().fold_batch_plan_codes_bytes(self.h))
+
+    def encode(self, seqs) -> np.ndarray:
+        """The batch's sequences as one concatenated code array (the layout fold_batch_dev reads)."""
+        assert [len(x) for x in seqs] == self.lens.tolist()
+        return np.concatenate([encode_codes(x) for x in seqs]) if len(seqs) else np.zeros(0, np.uint8)
+
+    def fold_dev(self, d_codes: int, d_ws: int, ws_bytes: int, d_max_pairs: int, stream: int | None = None) -> None:
+        _check(lib().fold_batch_dev(self.ctx, self.h, d_codes, d_ws, ws_bytes, d_max_pairs, stream), "fold_batch_dev")
+
+    def table_dev(self, d_ws: int, k: int, d_D_out: int, stream: int | None = None) -> None:
+        _check(lib().fold_batch_dev_table(self.ctx, self.h, d_ws, k, d_D_out, stream), "fold_batch_dev_table")
+
+    def close(self) -> None:
+        if self.h:
+            lib().fold_batch_plan_destroy(self.h)
+            self.h = None
 
 
 def fold_lookup_rate(device: int = 0, q: int = 8, mode: int = 0, iters: int = 4096):

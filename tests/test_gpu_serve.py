@@ -35,18 +35,28 @@ def test_serve_mix_equals_alone():
         kinds = ["uniform", "gc_rich", "structured"]
         lens = [0, 1, 2, 31, 32, 33, 100, 500, 1200, 64, 2500, 7, 300, 900]
         seqs = [synth.variant(kinds[k % 3], L, 900 + k) for k, L in enumerate(lens)]
-        alone = [f.score(s) for s in seqs]
+        alone = [f.score(s, want_D=True) for s in seqs]
         fold.fold_serve_start(f.ctx, 8 << 30, 64)
         tickets = []
+        tables = {}
         # staggered arrivals: some while others are already on the GPU
         for k, s in enumerate(seqs):
-            tickets.append(fold.fold_serve_submit(f.ctx, s))
+            t = fold.fold_serve_submit(f.ctx, s)
+            tickets.append(t)
+            if len(s):
+                tables[t] = np.full((len(s), len(s)), -1, dtype=np.int16)
             if k % 4 == 3:
                 time.sleep(0.002)
-        res = _drain(f.ctx, tickets)
+        res = _drain(f.ctx, tickets, want_D=tables)
         got = [res[t] for t in tickets]
-        assert got == alone
+        assert got == [a[0] for a in alone]
         assert got == [oracle.score(s) if len(s) else 0 for s in seqs]
+        # every full table folded in the mix equals the one folded alone and the oracle's (Eq. 1)
+        for t, s, (mp, D_alone) in zip(tickets, seqs, alone):
+            if not len(s):
+                continue
+            assert np.array_equal(tables[t], D_alone), len(s)
+            assert np.array_equal(tables[t].astype(np.int32), oracle.nussinov(s)), len(s)
         st = fold.fold_serve_stats(f.ctx)
         nonempty = sum(1 for s in seqs if len(s))
         assert st["admitted"] == st["finished"] == nonempty
