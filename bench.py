@@ -615,9 +615,10 @@ def main():
             barrier_sync()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            graph.replay()
-            e1.record(stream)
+            with torch.cuda.stream(stream):   # a graph replays on the current stream
+                e0.record(stream)
+                graph.replay()
+                e1.record(stream)
             e1.synchronize()
             gts.append(e0.elapsed_time(e1) / 1e3)
         for _ in range(3):

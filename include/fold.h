@@ -108,11 +108,16 @@ enum fold_option {
                                  the per-size task templates, kept by the context (up to 1 GiB; only a
                                  segment list is copied per call; default); 0 = built on the host and
                                  copied whole.  Results are identical. */
-    FOLD_OPT_COL_HELPERS = 17  /* single folds in column mode, two-vector: -1 = automatic (on where the
+    FOLD_OPT_COL_HELPERS = 17, /* single folds in column mode, two-vector: -1 = automatic (on where the
                                   layout has at most 4 columns per tile CTA), 1 = on, 0 = off.  On, warp
                                   w + 4 of each tile CTA helps column warp w: it loads each tile's inputs,
                                   does its late middle blocks' lookups and the chunk merge, and publishes
                                   each finished tile, so the column warp only computes rows */
+    FOLD_OPT_SERVE_RING = 18   /* serving: 1 (default) = requests in flight are folded by one persistent
+                                  launch fed while it runs (a task ring the serving thread fills round
+                                  by round); 0 = repeated launches, each a slice of tile diagonals of
+                                  every request.  Set before fold_serve_start (FOLD_EAGAIN while
+                                  serving).  Results are identical. */
 };
 
 /* One record per task of the last traced persistent launch. */
@@ -376,15 +381,26 @@ int fold_batch_dev_table(fold_ctx *ctx, const fold_batch_plan *plan, const void 
 /* Serving (continuous batching).  fold_serve_start starts a host scheduler
  * thread that admits submitted requests while the device memory their two
  * int16 D copies need (about 4*n^2 bytes each) fits `budget_bytes` and at
- * most `max_inflight` are in flight, and folds the admitted set in repeated
- * persistent launches, each advancing every in-flight request by a slice of
- * tile diagonals; requests that arrive while others are on the GPU join at
- * the next slice.  fold_serve_submit copies the sequence and returns a ticket
- * (FOLD_EAGAIN if the request alone exceeds the budget or the queue is
- * full).  fold_serve_poll returns FOLD_ENOTREADY while in flight and FOLD_OK
- * once done, filling max_pairs (and D_out, n*n int16, if not NULL); the ticket
- * is then released.  fold_serve_stop drains nothing: in-flight requests are
- * abandoned and their tickets become invalid. */
+ * most `max_inflight` are in flight.  A request arriving to an idle server
+ * (n <= 8192) folds alone in one launch with the single fold's work split.
+ * Otherwise the in-flight requests are folded by one persistent launch that
+ * the thread feeds while it runs (FOLD_OPT_SERVE_RING, default): round after
+ * round it publishes the next tile diagonal of every in-flight request into a
+ * device task ring, so a request that arrives while others are on the GPU
+ * joins at the next round, with no launch boundary to wait for; answers come
+ * back through host-mapped memory, and the launch ends when nothing is in
+ * flight.  While that launch runs it holds every SM: other kernels of the
+ * process (folds on any context) start once the server is idle.  With
+ * FOLD_OPT_SERVE_RING = 0 the requests are folded in repeated launches, each
+ * advancing every in-flight request by a slice of tile diagonals.  Every warp
+ * of a slice takes tile and chunk tasks from one queue, unless
+ * FOLD_OPT_NEAR_CTAS was set above 0 when serving started (that many CTAs
+ * then take only tile tasks).  fold_serve_submit copies the sequence and
+ * returns a ticket (FOLD_EAGAIN if the request alone exceeds the budget or the
+ * queue is full).  fold_serve_poll returns FOLD_ENOTREADY while in flight and
+ * FOLD_OK once done, filling max_pairs (and D_out, n*n int16, if not NULL);
+ * the ticket is then released.  fold_serve_stop drains nothing: in-flight
+ * requests are abandoned and their tickets become invalid. */
 int fold_serve_start(fold_ctx *ctx, int64_t budget_bytes, int32_t max_inflight);
 int fold_serve_submit(fold_ctx *ctx, const char *seq, int32_t n, uint64_t *ticket);
 int fold_serve_poll(fold_ctx *ctx, uint64_t ticket, int32_t *max_pairs, int16_t *D_out);
@@ -409,13 +425,13 @@ int fold_serve_warm(fold_ctx *ctx, int32_t max_n);
 /* Counters of the serving loop since fold_serve_start (for monitoring and
  * tuning).  A "slice" is one persistent launch over the in-flight set. */
 typedef struct fold_serve_stats {
-    uint64_t slices;        /* persistent launches so far */
-    uint64_t tasks;         /* tasks those launches ran */
+    uint64_t slices;        /* persistent launches so far (lone requests, serving-ring launches, slices) */
+    uint64_t tasks;         /* tasks those launches ran (on the ring: tasks published) */
     uint64_t admitted;      /* requests admitted into the device arena */
     uint64_t finished;      /* requests done or failed */
-    double gpu_ms;          /* device time of the slices (CUDA events around each launch) */
-    double slice_ms;        /* host wall time from a slice's first enqueue to its results on the host */
-    double prep_ms;         /* host time gathering slices' task lists and descriptors */
+    double gpu_ms;          /* device time of the launches (CUDA events around each launch) */
+    double slice_ms;        /* host wall time from a launch's first enqueue to its results on the host */
+    double prep_ms;         /* host time gathering task lists, descriptors and (ring) copies */
     int32_t queued;         /* waiting for admission now */
     int32_t inflight;       /* on the device now */
     uint64_t solo;          /* requests that arrived to an idle server (nothing else in flight or

@@ -740,6 +740,11 @@ int fold_set_option(fold_ctx *ctx, int option, int64_t value) {
             if (value < -1 || value > 1) return FOLD_EINVAL;
             ctx->col_helpers_opt = (int)value;
             return FOLD_OK;
+        case FOLD_OPT_SERVE_RING:
+            if (value < 0 || value > 1) return FOLD_EINVAL;
+            if (ctx->serve) return FOLD_EAGAIN;
+            ctx->serve_ring = (int)value;
+            return FOLD_OK;
         case FOLD_OPT_BATCH_FLAT:
             if (value < -1 || value > 1) return FOLD_EINVAL;
             ctx->batch_flat_opt = (int)value;
@@ -773,6 +778,7 @@ int fold_get_option(fold_ctx *ctx, int option, int64_t *value) {
         case FOLD_OPT_NEAR_CTAS: *value = ctx->near_ctas_opt; return FOLD_OK;
         case FOLD_OPT_COLUMNS: *value = ctx->columns_opt; return FOLD_OK;
         case FOLD_OPT_COL_HELPERS: *value = ctx->col_helpers_opt; return FOLD_OK;
+        case FOLD_OPT_SERVE_RING: *value = ctx->serve_ring; return FOLD_OK;
         case FOLD_OPT_BATCH_FLAT: *value = ctx->batch_flat_opt; return FOLD_OK;
         case FOLD_OPT_R_MEMO: *value = ctx->r_memo; return FOLD_OK;
         case FOLD_OPT_BATCH_GATHER: *value = ctx->batch_gather; return FOLD_OK;

@@ -69,6 +69,7 @@ struct fold_ctx {
     int near_ctas_opt = -1;    // -1 automatic, 0 one shared queue, k > 0 k tile-only CTAs
     int columns_opt = -1;      // -1 automatic, 0 off, v >= 1 column mode with v columns per tile CTA
     int col_helpers_opt = -1;  // FOLD_OPT_COL_HELPERS: -1 automatic, 0 off, 1 on (column mode, two-vector)
+    int serve_ring = 1;        // FOLD_OPT_SERVE_RING: serving through one persistent launch fed while it runs
     int batch_flat_opt = -1;   // fold_batch chunks: -1 / 1 kc blocks each, 0 geometric sizes
     int batch_gather = 1;      // FOLD_OPT_BATCH_GATHER: fold_batch's list gathered on the device
     int r_memo = 0;            // FOLD_OPT_R_MEMO: tabulate R rows on first sight (two-vector, q <= 9)

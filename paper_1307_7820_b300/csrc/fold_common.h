@@ -101,6 +101,16 @@ struct FoldParams {
     unsigned long long pair64;  // bit (8x+y) = b(x,y)
     long long timeout_ns;     // bound on every device-side wait
     long long *trace;         // optional: kTraceWords words per task (see fold_trace_rec), or nullptr
+    // serving ring (one persistent launch fed while it runs): ring_cap > 0 means task i is at
+    // tasks[i % ring_cap] and exists once i < *ring_tail; the host advances *ring_tail (by copies, after
+    // the tasks) and sets *ring_stop when it will publish no more; a worker whose claimed index is not
+    // published waits (bounded) and leaves when the stop word is set.  Workers record the claimed
+    // index in *ring_progress (host-mapped) every 256 claims, and answers go to host-mapped `results`
+    // behind a system-scope fence.
+    int ring_cap;
+    const int *ring_tail;
+    const int *ring_stop;
+    int *ring_progress;
 };
 
 // error word values written by the kernel

@@ -514,7 +514,9 @@ struct NextTask {
     int idx;
     int4 tk;
     bool have;
+    bool stopped;  // serving ring: the host stopped publishing and this claim has no task
     int pending;   // lane 0: the queue atomic's result, read by finish()
+    const FoldParams *P;
     // the queue atomic goes out here; its result is read by finish()
     __device__ __forceinline__ void start(int lane) {
         if (lane == 0) pending = atomicAdd(qhead, 1);
@@ -522,8 +524,43 @@ struct NextTask {
     __device__ __forceinline__ void finish(int lane) {
         const int i = qbase + __shfl_sync(FULL, lane == 0 ? pending : 0, 0);
         idx = i;
-        tk = i < qlimit ? tasks[i] : make_int4(0, 0, 0, 0);
+        // serving ring: the task is fetched by fetch() once the current task is complete (a chunk
+        // claims its successor before it counts itself done, and the successor may not be published)
+        tk = (P->ring_cap == 0 && i < qlimit) ? tasks[i] : make_int4(0, 0, 0, 0);
         have = true;
+    }
+    // serving ring: wait until the claimed task is published (or the host stopped), then load it
+    __device__ __forceinline__ void fetch(int lane) {
+        if (P->ring_cap == 0) return;
+        ring_wait(lane);
+        tk = stopped ? make_int4(0, 0, 0, 0) : __ldcg(tasks + (idx % P->ring_cap));
+        if (lane == 0 && (idx & 255) == 0) *(volatile int *)P->ring_progress = idx;
+    }
+    // serving ring: wait (bounded) until the claimed index is published or the host has stopped
+    __device__ __noinline__ void ring_wait(int lane) {
+        int st = 0;
+        if (lane == 0 && ld_acquire(P->ring_tail) <= idx) {
+            const unsigned long long t0 = gtimer();
+            unsigned ns = 0;
+            for (;;) {
+                if (ld_acquire(P->ring_tail) > idx) break;
+                if (ld_acquire(P->ring_stop) != 0) {
+                    if (ld_acquire(P->ring_tail) > idx) break;
+                    st = 1;
+                    break;
+                }
+                if (*(volatile int *)P->error != 0) { st = 1; break; }
+                if ((long long)(gtimer() - t0) > P->timeout_ns) {
+                    atomicCAS(P->error, 0, kErrTimeout);
+                    st = 1;
+                    break;
+                }
+                __nanosleep(ns);
+                ns = ns ? (ns < 1024 ? 2 * ns : 1024) : 64;
+            }
+        }
+        stopped = __shfl_sync(FULL, st, 0) != 0;
+        __syncwarp();
     }
     __device__ __forceinline__ void claim(int lane) {
         start(lane);
@@ -1533,10 +1570,20 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll 8
         for (int cc = 0; cc < T; ++cc) Dcol[(size_t)(JT + cc) * PC + IT + lane + kColOff] = tile[lane][cc];
     }
-    // answer D(0, n-1)
+    // answer D(0, n-1); on the serving ring it goes to host memory, after a system-scope fence that
+    // makes the table (this warp's rows, and the other tiles it acquired) visible to the host's copies
     if (I == 0 && J == NT - 1) {
         const int cn = (sd.n - 1) - JT;
-        if (sd.n >= 1 && lane == cn) P.results[sd.result_index] = (sd.n >= 2) ? (int)tile[0][cn] : 0;
+        if (P.ring_cap > 0) __syncwarp();
+        if (sd.n >= 1 && lane == cn) {
+            const int v = (sd.n >= 2) ? (int)tile[0][cn] : 0;
+            if (P.ring_cap > 0) {
+                __threadfence_system();
+                *(volatile int *)(P.results + sd.result_index) = v;
+            } else {
+                P.results[sd.result_index] = v;
+            }
+        }
     }
     if constexpr (COL) {
         // carry the column's constants and the bottom row to the next tile of this column
@@ -1729,16 +1776,19 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
     NextTask nt;
     nt.qhead = far_role ? P.queue_head_far : P.queue_head;
     nt.qbase = far_role ? P.nnear : 0;
-    nt.qlimit = (split && !far_role) ? P.nnear : P.ntasks;
+    nt.qlimit = P.ring_cap > 0 ? 0x7fffffff : ((split && !far_role) ? P.nnear : P.ntasks);
     nt.tasks = P.tasks;
     nt.have = false;
+    nt.stopped = false;
+    nt.P = &P;
     int err = 0;   // the error word as read when the previous task started
     for (;;) {
         if (!nt.have) nt.claim(lane);
         nt.have = false;
+        nt.fetch(lane);
         const int idx = nt.idx;
         const int4 tk = nt.tk;
-        if (idx >= nt.qlimit || err != 0) break;
+        if (idx >= nt.qlimit || err != 0 || nt.stopped) break;
         err = ld_relaxed(P.error);   // checked before the next task
         const SeqDesc sd = P.seqs[tk.x];
         const int I = task_I(tk.y), J = task_J(tk.y);

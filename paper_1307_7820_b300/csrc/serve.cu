@@ -3,12 +3,20 @@
 // A host scheduler thread owns one device arena of `budget_bytes`.  Submitted
 // requests wait in a FIFO until their workspace (D copies, difference
 // vectors, tile flags: the single-sequence plan) fits the arena and fewer
-// than `max_inflight` requests are in flight.  The thread then folds every
-// in-flight request in repeated persistent launches; each launch runs, for
-// every request, the tasks of its next kSlice tile diagonals (the same
-// ordered task list a single fold uses, cut at step boundaries), so requests
-// admitted while others are running join the next launch and share the GPU
-// with them.  All in-flight DP state stays in the arena between launches.  A
+// than `max_inflight` requests are in flight.  A request arriving to an idle
+// server (up to kSoloMaxN bases) folds alone in one launch with the single
+// fold's work split.  Otherwise the in-flight requests are folded by one
+// persistent launch fed while it runs (the serving ring): the thread
+// publishes, round after round, the next tile diagonal of every in-flight
+// request's task list (the ordered list a single fold uses) into a device
+// ring by copies, and advances the ring's tail; the launch's warps take tasks
+// in ring order, each waiting (bounded) only on tasks of its own request
+// published before it.  A request admitted meanwhile joins the next round, so
+// no request waits for a launch boundary.  Answers come back through
+// host-mapped memory; when nothing is in flight the thread stops the launch.
+// With the ring switched off (FOLD_OPT_SERVE_RING = 0) the in-flight requests
+// are folded in repeated launches instead, each advancing every request by a
+// slice of tile diagonals.  All in-flight DP state stays in the arena.  A
 // finished request keeps its block until its ticket is polled.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -40,6 +48,9 @@ constexpr double kSliceTargetMs = 2.0;
 constexpr int kSoloMaxN = 8192;      // a lone request up to this length folds in one launch (~3.5 ms)
 constexpr size_t kMaxQueued = 1 << 20;
 constexpr size_t kLaunchBytes0 = size_t(16) << 20;   // initial launch-list buffers (host and device)
+constexpr int kRingCap = 1 << 22;    // serving ring: tasks (64 MiB)
+constexpr long long kRingAhead = 8192;   // tasks published ahead of the claims the launch reported
+constexpr int kResultPending = INT32_MIN;
 
 struct Request {
     uint64_t ticket = 0;
@@ -54,6 +65,7 @@ struct Request {
     int state = 0;                   // 0 queued, 1 in flight, 2 done, 3 failed
     int status = FOLD_OK;
     int32_t result = 0;
+    int slot = -1;                   // serving ring: index of its descriptor and answer
 };
 
 // first-fit allocator over [0, size) in 256-byte units
@@ -116,6 +128,22 @@ struct ServeState {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     unsigned long long launches = 0;
     fold_serve_stats stats{};        // guarded by mu
+    int near_ctas = 0;               // slices: tile-only CTAs (0: one shared queue)
+    std::vector<int4> split_tmp;     // chunk tasks while a slice's list is split
+    // serving ring
+    bool use_ring = true;
+    bool ring_on = false;            // a ring launch is running
+    int ring_slots = 0;              // descriptors / answers (max_inflight)
+    DevBuf d_ring;                   // control words | SeqDesc[ring_slots] | tasks[kRingCap]
+    int *h_map = nullptr;            // host-mapped: answers[ring_slots] | reported claim index
+    int *d_map = nullptr;            // its device address
+    HostBuf h_stage;                 // pinned: a round's tasks, descriptors, codes, tail values
+    HostBuf h_zero;                  // pinned zeros (a request's control region is cleared by a copy)
+    cudaStream_t cst = nullptr;      // copies into the running launch
+    cudaEvent_t ring_ev0 = nullptr, ring_ev1 = nullptr;
+    long long ring_tail = 0;         // tasks published
+    std::vector<int> free_slots;
+    std::chrono::steady_clock::time_point ring_t0;
 };
 
 static size_t al256(size_t v) { return (v + 255) / 256 * 256; }
@@ -159,6 +187,293 @@ static void fail_inflight(ServeState *S, int status) {
     S->inflight.clear();
 }
 
+
+// ---------------------------------------------------------------- serving ring
+// Device layout of d_ring: control words (queue head, error, tail, stop) | SeqDesc per slot | tasks.
+static constexpr size_t kRingCtrl = 256;
+static size_t ring_o_sd() { return kRingCtrl; }
+static size_t ring_o_tasks(const ServeState *S) { return al256(kRingCtrl + sizeof(SeqDesc) * (size_t)S->ring_slots); }
+static constexpr size_t kStageBytes = size_t(32) << 20;   // pinned staging per batch of copies
+static constexpr size_t kZeroBytes = size_t(16) << 20;    // pinned zeros, copied as often as needed
+
+// Resources for the ring, made when serving starts (nothing here may allocate or free while a ring
+// launch runs: those calls can wait for the device, which waits for this thread).
+static int ring_setup(ServeState *S) {
+    S->ring_slots = S->max_inflight;
+    const size_t bytes = ring_o_tasks(S) + sizeof(int4) * (size_t)kRingCap;
+    if (ensure_buf(S->d_ring, bytes)) return FOLD_ENOMEM;
+    if (cudaHostAlloc(reinterpret_cast<void **>(&S->h_map), sizeof(int) * ((size_t)S->ring_slots + 64),
+                      cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        return FOLD_ENOMEM;
+    }
+    if (cudaHostGetDevicePointer(reinterpret_cast<void **>(&S->d_map), S->h_map, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return FOLD_ECUDA;
+    }
+    if (ensure_host(S->h_stage, kStageBytes) || ensure_host(S->h_zero, kZeroBytes)) return FOLD_ENOMEM;
+    memset(S->h_zero.ptr, 0, kZeroBytes);
+    if (cudaStreamCreateWithFlags(&S->cst, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&S->ring_ev0) != cudaSuccess || cudaEventCreate(&S->ring_ev1) != cudaSuccess) {
+        cudaGetLastError();
+        return FOLD_ECUDA;
+    }
+    S->free_slots.clear();
+    for (int k = S->ring_slots - 1; k >= 0; --k) S->free_slots.push_back(k);
+    return FOLD_OK;
+}
+
+static void ring_teardown(ServeState *S) {
+    if (S->cst) cudaStreamDestroy(S->cst);
+    if (S->ring_ev0) cudaEventDestroy(S->ring_ev0);
+    if (S->ring_ev1) cudaEventDestroy(S->ring_ev1);
+    if (S->h_map) cudaFreeHost(S->h_map);
+    if (S->h_stage.ptr) cudaFreeHost(S->h_stage.ptr);
+    if (S->h_zero.ptr) cudaFreeHost(S->h_zero.ptr);
+    if (S->d_ring.ptr) cudaFree(S->d_ring.ptr);
+}
+
+// One persistent launch over the ring, on S->st (its control words cleared first: no launch runs).
+static cudaError_t ring_start(ServeState *S) {
+    fold_ctx *ctx = S->ctx;
+    uint8_t *base = reinterpret_cast<uint8_t *>(S->d_ring.ptr);
+    int *ctrl = reinterpret_cast<int *>(base);
+    // cleared before any copy of the copy stream can reach the control words (the tail)
+    cudaError_t e = cudaMemsetAsync(ctrl, 0, kRingCtrl, S->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
+    reinterpret_cast<volatile int *>(S->h_map)[S->ring_slots] = 0;   // claim index reported so far
+    FoldParams p;
+    memset(&p, 0, sizeof p);
+    p.tasks = reinterpret_cast<const int4 *>(base + ring_o_tasks(S));
+    p.ntasks = 0;
+    p.queue_head = ctrl;
+    p.error = ctrl + 1;
+    p.queue_head_far = ctrl + 4;
+    p.seqs = reinterpret_cast<const SeqDesc *>(base + ring_o_sd());
+    p.codes = S->arena_base;
+    p.drow = reinterpret_cast<int16_t *>(S->arena_base);
+    p.dcol = reinterpret_cast<int16_t *>(S->arena_base);
+    p.rf = reinterpret_cast<uint32_t *>(S->arena_base);
+    p.cf = reinterpret_cast<uint32_t *>(S->arena_base);
+    p.flags = reinterpret_cast<int *>(S->arena_base);
+    p.cnt = reinterpret_cast<int *>(S->arena_base);
+    p.pring = reinterpret_cast<int *>(S->arena_base);
+    p.results = S->d_map;
+    p.rtab = ctx->d_rpacked;
+    p.pair64 = ctx->pair64;
+    p.memo = (ctx->r_memo && ctx->method == kTwoVector) ? 1 : 0;
+    p.timeout_ns = ctx->timeout_ms * 1000000LL;
+    p.ring_cap = kRingCap;
+    p.ring_tail = ctrl + 2;
+    p.ring_stop = ctrl + 3;
+    p.ring_progress = S->d_map + S->ring_slots;
+    if (e == cudaSuccess) e = cudaEventRecord(S->ring_ev0, S->st);
+    if (e == cudaSuccess) e = launch_fold(p, ctx->q, ctx->method, grid_for(ctx), S->st);
+    if (e == cudaSuccess) e = cudaEventRecord(S->ring_ev1, S->st);
+    if (e == cudaSuccess) {
+        S->ring_on = true;
+        S->ring_tail = 0;
+        S->launches += 1;
+        S->ring_t0 = std::chrono::steady_clock::now();
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stats.slices++;
+    }
+    return e;
+}
+
+// Copies `bytes` from pinned staging (or zeros) to the device on the copy stream, in pieces the
+// pinned buffers hold; the caller synchronises the copy stream before reusing the staging.
+static cudaError_t ring_zero(ServeState *S, uint8_t *dst, size_t bytes) {
+    cudaError_t e = cudaSuccess;
+    for (size_t o = 0; o < bytes && e == cudaSuccess; o += kZeroBytes)
+        e = cudaMemcpyAsync(dst + o, S->h_zero.ptr, std::min(kZeroBytes, bytes - o), cudaMemcpyHostToDevice, S->cst);
+    return e;
+}
+
+// A newly admitted request on the ring: its slot, answer word, descriptor, cleared control region and
+// codes (copies on the copy stream, all before any of its tasks is published).
+static cudaError_t ring_admit(ServeState *S, Request &r, uint8_t *stage, size_t *used) {
+    r.slot = S->free_slots.back();
+    S->free_slots.pop_back();
+    reinterpret_cast<volatile int *>(S->h_map)[r.slot] = kResultPending;
+    uint8_t *base = S->arena_base + r.block;
+    SeqDesc d = arena_desc(r, r.slot);
+    const size_t need = al256(sizeof(SeqDesc)) + al256(r.codes.size());
+    if (*used + need > kStageBytes) {   // staging full: let the copies queued so far finish
+        cudaError_t e = cudaStreamSynchronize(S->cst);
+        if (e != cudaSuccess) return e;
+        *used = 0;
+    }
+    uint8_t *hs = stage + *used;
+    memcpy(hs, &d, sizeof d);
+    memcpy(hs + al256(sizeof(SeqDesc)), r.codes.data(), r.codes.size());
+    *used += need;
+    uint8_t *dsd = reinterpret_cast<uint8_t *>(S->d_ring.ptr) + ring_o_sd() + sizeof(SeqDesc) * (size_t)r.slot;
+    cudaError_t e = cudaMemcpyAsync(dsd, hs, sizeof(SeqDesc), cudaMemcpyHostToDevice, S->cst);
+    if (e == cudaSuccess) e = ring_zero(S, base, r.pl.zero_bytes);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + r.pl.off_codes, hs + al256(sizeof(SeqDesc)), r.codes.size(), cudaMemcpyHostToDevice, S->cst);
+    return e;
+}
+
+// Publishes rounds (the next tile diagonal of every in-flight request, in admission order) while
+// fewer than kRingAhead tasks are published beyond the claims the launch reported; returns the tasks
+// published.
+static long long ring_publish(ServeState *S, const std::vector<Request *> &active, uint8_t *stage, size_t used,
+                              cudaError_t *err) {
+    const long long claimed = reinterpret_cast<volatile int *>(S->h_map)[S->ring_slots];
+    int4 *buf = reinterpret_cast<int4 *>(stage + al256(used));
+    const size_t cap = (kStageBytes - al256(used) - 256) / sizeof(int4);
+    size_t m = 0;
+    // one diagonal of every request per round (a round's tasks are mostly ready to run when claimed:
+    // more diagonals per round for long requests filled the queue with waiting chunks and collapsed the
+    // throughput at 2000 req/s), the requests with the most diagonals left first, so the long ones,
+    // whose chains set the tail latency, are claimed at the head of each round
+    std::vector<Request *> order(active.begin(), active.end());
+    std::stable_sort(order.begin(), order.end(),
+                     [](const Request *x, const Request *y) { return x->NT - x->cursor > y->NT - y->cursor; });
+    bool any = true;
+    while (any && S->ring_tail + (long long)m - claimed < kRingAhead) {
+        any = false;
+        for (Request *r : order) {
+            if (r->cursor >= r->NT) continue;
+            const int steps = 1;
+            const SeqTemplate &sc = *r->sched;
+            const int a = sc.near_begin[r->cursor], b = sc.near_begin[r->cursor + steps];
+            if (m + (size_t)(b - a) > cap) break;
+            for (int q = a; q < b; ++q) {
+                int4 tk = sc.tasks[q];
+                tk.x = r->slot;
+                buf[m++] = tk;
+            }
+            r->cursor += steps;
+            any = true;
+        }
+    }
+    if (m == 0) return 0;
+    int4 *ring = reinterpret_cast<int4 *>(reinterpret_cast<uint8_t *>(S->d_ring.ptr) + ring_o_tasks(S));
+    const size_t at = (size_t)(S->ring_tail % kRingCap);
+    const size_t first = std::min(m, (size_t)kRingCap - at);
+    cudaError_t e = cudaMemcpyAsync(ring + at, buf, sizeof(int4) * first, cudaMemcpyHostToDevice, S->cst);
+    if (e == cudaSuccess && first < m)
+        e = cudaMemcpyAsync(ring, buf + first, sizeof(int4) * (m - first), cudaMemcpyHostToDevice, S->cst);
+    int *tail_src = reinterpret_cast<int *>(buf + m);
+    *tail_src = (int)(S->ring_tail + (long long)m);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(reinterpret_cast<int *>(S->d_ring.ptr) + 2, tail_src, sizeof(int), cudaMemcpyHostToDevice, S->cst);
+    *err = e;
+    if (e == cudaSuccess) S->ring_tail += (long long)m;
+    return (long long)m;
+}
+
+// Fails every in-flight request of the ring and frees their slots.
+static void ring_fail(ServeState *S, int status) {
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (uint64_t t : S->inflight) {
+            auto it = S->reqs.find(t);
+            if (it != S->reqs.end() && it->second.slot >= 0) S->free_slots.push_back(it->second.slot);
+        }
+    }
+    fail_inflight(S, status);
+}
+
+// Stops the ring launch (no more tasks) and waits for it; returns its error word.
+static int ring_stop(ServeState *S) {
+    int *stop_src = reinterpret_cast<int *>(S->h_stage.ptr);
+    *stop_src = 1;
+    cudaError_t e = cudaMemcpyAsync(reinterpret_cast<int *>(S->d_ring.ptr) + 3, stop_src, sizeof(int),
+                                    cudaMemcpyHostToDevice, S->cst);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->cst);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&err, reinterpret_cast<int *>(S->d_ring.ptr) + 1, sizeof(int), cudaMemcpyDeviceToHost);
+    S->ring_on = false;
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, S->ring_ev0, S->ring_ev1);
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stats.gpu_ms += ms;
+    S->stats.slice_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - S->ring_t0).count();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return kErrTimeout;
+    }
+    return err;
+}
+
+// One pass of the ring loop over the in-flight requests: admit the new ones, publish rounds, collect
+// answers; the launch starts when needed and stops when nothing is in flight.
+static void ring_iteration(ServeState *S, const std::vector<uint64_t> &admitted, std::vector<Request *> &active) {
+    cudaError_t e = cudaSuccess;
+    uint8_t *stage = reinterpret_cast<uint8_t *>(S->h_stage.ptr) + 256;   // the first 256 bytes: the stop word
+    size_t used = 0;
+    const auto t_prep = std::chrono::steady_clock::now();
+    for (uint64_t t : admitted) {
+        Request *r;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            r = &S->reqs[t];
+        }
+        if (e == cudaSuccess) e = ring_admit(S, *r, stage, &used);
+    }
+    if (e == cudaSuccess && !S->ring_on) e = ring_start(S);
+    long long pub = 0;
+    if (e == cudaSuccess) pub = ring_publish(S, active, stage, used, &e);
+    if (e == cudaSuccess && (used || pub)) e = cudaStreamSynchronize(S->cst);   // the staging is free again
+    const auto t_pub = std::chrono::steady_clock::now();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (S->ring_on) ring_stop(S);
+        ring_fail(S, FOLD_ECUDA);
+        return;
+    }
+    // answers (host-mapped, written behind a system-scope fence by each request's last tile)
+    const volatile int *ans = S->h_map;
+    bool launch_ended = cudaEventQuery(S->ring_ev1) == cudaSuccess;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stats.tasks += (uint64_t)pub;
+        S->stats.admitted += admitted.size();
+        S->stats.prep_ms += std::chrono::duration<double, std::milli>(t_pub - t_prep).count();
+        std::vector<uint64_t> still;
+        for (uint64_t t : S->inflight) {
+            Request &r = S->reqs[t];
+            const int v = ans[r.slot];
+            if (v != kResultPending) {
+                if (v < 0) {
+                    r.state = 3;
+                    r.status = FOLD_ECUDA;
+                } else {
+                    r.state = 2;
+                    r.result = r.n >= 2 ? v : 0;
+                }
+                S->free_slots.push_back(r.slot);
+                S->stats.finished++;
+                mark_done(S, t);
+            } else {
+                still.push_back(t);
+            }
+        }
+        S->inflight.swap(still);
+        launch_ended = launch_ended && !S->inflight.empty();
+    }
+    if (launch_ended) {   // the launch left with requests unanswered: a bounded wait expired
+        const int err = ring_stop(S);
+        ring_fail(S, err == kErrTimeout ? FOLD_ETIMEOUT : FOLD_ECUDA);
+        return;
+    }
+    bool idle;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        idle = S->inflight.empty() && S->queued.empty();
+    }
+    if (idle) {
+        ring_stop(S);
+        return;
+    }
+    if (!pub && admitted.empty()) std::this_thread::sleep_for(std::chrono::microseconds(20));
+}
+
 static void serve_loop(ServeState *S) {
     fold_ctx *ctx = S->ctx;
     cudaSetDevice(ctx->device);
@@ -185,7 +500,24 @@ static void serve_loop(ServeState *S) {
             }
             for (uint64_t t : S->inflight) active.push_back(&S->reqs[t]);
         }
-        if (active.empty()) continue;
+        if (active.empty()) {
+            if (S->ring_on) ring_stop(S);   // nothing to publish: the launch must not wait for tasks
+            continue;
+        }
+        // a request alone in the system (just admitted, nothing else in flight or waiting) folds in
+        // one launch with the single-fold work split (column mode where it applies), as
+        // fold_score_dev would, instead of on the ring or slice by slice in the one-queue layout; up
+        // to kSoloMaxN, so that a request arriving meanwhile waits at most about that fold's time
+        bool solo = false;
+        if (!S->ring_on && active.size() == 1 && admitted.size() == 1 && active[0]->cursor == 0 &&
+            active[0]->n >= 2 && active[0]->n <= kSoloMaxN) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            solo = S->queued.empty();
+        }
+        if (S->use_ring && !solo) {
+            ring_iteration(S, admitted, active);
+            continue;
+        }
         const auto t_prep = std::chrono::steady_clock::now();
         // new requests: zeroed control/flag region and padded codes
         cudaError_t e = cudaSuccess;
@@ -201,17 +533,7 @@ static void serve_loop(ServeState *S) {
                 e = cudaMemcpyAsync(base + r->pl.off_codes, r->codes.data(), r->codes.size(), cudaMemcpyHostToDevice, S->st);
             // the host copy of the codes must stay alive until this copy ran: synchronised below
         }
-        // a request alone in the system (just admitted, nothing else in flight or waiting) folds in
-        // one launch with the single-fold work split (column mode where it applies), as
-        // fold_score_dev would, instead of slice by slice in the one-queue layout; up to
-        // kSoloMaxN, so that a request arriving meanwhile waits at most about that fold's time
-        bool solo = false;
-        if (e == cudaSuccess && active.size() == 1 && admitted.size() == 1 && active[0]->cursor == 0 &&
-            active[0]->n >= 2 && active[0]->n <= kSoloMaxN) {
-            std::lock_guard<std::mutex> lk(S->mu);
-            solo = S->queued.empty();
-        }
-        if (solo) {
+        if (solo && e == cudaSuccess) {
             Request &r = *active[0];
             const SeqTemplate &sc = *r.sched;
             const FoldOpts o;   // automatic work split, whatever the caller's options
@@ -336,6 +658,26 @@ static void serve_loop(ServeState *S) {
                 dst += b - a;
             }
         }
+        // with tile-only CTAs (FOLD_OPT_NEAR_CTAS > 0 when serving started) the slice's list becomes
+        // [tile tasks | chunk tasks], each part in list order; both queues are taken in order and a
+        // task waits only on tasks before it in the list, so progress is kept as for a single fold's
+        // split layout.  Measured slower than one shared queue at 1000-2000 req/s (p99 17 and 41 ms
+        // against 10 and 14 ms: the chunk CTAs fall behind), so not the default
+        int nnear = 0;
+        const int grid = grid_for(ctx);
+        const int near_ctas = S->near_ctas;
+        const bool split = near_ctas > 0 && near_ctas < grid && ntasks > 0;
+        if (split) {
+            int4 *all = reinterpret_cast<int4 *>(h + o_tasks);
+            S->split_tmp.resize(ntasks);
+            int4 *far = S->split_tmp.data();
+            size_t nf = 0;
+            for (size_t q = 0; q < ntasks; ++q) {
+                if (task_type(all[q].y) == kTaskNear) all[nnear++] = all[q];
+                else far[nf++] = all[q];
+            }
+            memcpy(all + nnear, far, sizeof(int4) * nf);
+        }
         if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, o_sd, S->st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d + o_sd, h + o_sd, o_out - o_sd, cudaMemcpyHostToDevice, S->st);
         FoldParams p;
@@ -345,8 +687,8 @@ static void serve_loop(ServeState *S) {
         p.queue_head = reinterpret_cast<int *>(d);
         p.error = reinterpret_cast<int *>(d) + 1;
         p.queue_head_far = reinterpret_cast<int *>(d) + 2;
-        p.nnear = 0;
-        p.near_ctas = 0;
+        p.nnear = split ? nnear : 0;
+        p.near_ctas = split ? near_ctas : 0;
         p.seqs = reinterpret_cast<const SeqDesc *>(d + o_sd);
         p.codes = S->arena_base;
         p.drow = reinterpret_cast<int16_t *>(S->arena_base);
@@ -428,6 +770,7 @@ int fold_serve_start(fold_ctx *ctx, int64_t budget_bytes, int32_t max_inflight) 
     S->ctx = ctx;
     S->budget = (size_t)budget_bytes;
     S->max_inflight = max_inflight;
+    S->near_ctas = ctx->near_ctas_opt > 0 ? ctx->near_ctas_opt : 0;
     if (cudaMalloc(&S->arena_base, S->budget) != cudaSuccess) {
         cudaGetLastError();
         delete S;
@@ -455,6 +798,22 @@ int fold_serve_start(fold_ctx *ctx, int64_t budget_bytes, int32_t max_inflight) 
         cudaFree(S->arena_base);
         delete S;
         return FOLD_ENOMEM;
+    }
+    S->use_ring = ctx->serve_ring != 0;
+    if (S->use_ring) {
+        const int rc = ring_setup(S);
+        if (rc) {
+            ring_teardown(S);
+            if (S->d_launch.ptr) cudaFree(S->d_launch.ptr);
+            if (S->h_launch.ptr) cudaFreeHost(S->h_launch.ptr);
+            cudaEventDestroy(S->ev0);
+            cudaEventDestroy(S->ev1);
+            cudaStreamDestroy(S->st);
+            cudaStreamDestroy(S->poll_st);
+            cudaFree(S->arena_base);
+            delete S;
+            return rc;
+        }
     }
     ctx->serve = S;
     S->th = std::thread(serve_loop, S);
@@ -533,17 +892,20 @@ int fold_serve_poll(fold_ctx *ctx, uint64_t ticket, int32_t *max_pairs, int16_t 
     int status = r.state == 2 ? FOLD_OK : r.status;
     if (status == FOLD_OK) *max_pairs = r.result;
     if (status == FOLD_OK && D_out && r.n > 0) {
+        // rows of the padded row-major table straight to the caller's buffer by the copy engine (no
+        // kernel and no allocation: a ring launch may hold every SM), then the lower triangle, which
+        // the fold never writes, set to zero
         cudaSetDevice(ctx->device);
-        int16_t *dd = nullptr;
-        size_t bytes = (size_t)r.n * r.n * 2;
-        cudaError_t e = cudaMalloc(&dd, bytes);
-        if (e == cudaSuccess)
-            e = launch_extract(reinterpret_cast<int16_t *>(S->arena_base + r.block + r.pl.off_drow), r.pl.sd[0].Np, r.n, dd,
-                               S->poll_st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(D_out, dd, bytes, cudaMemcpyDeviceToHost, S->poll_st);
+        const size_t n = (size_t)r.n;
+        cudaError_t e = cudaMemcpy2DAsync(D_out, n * 2, S->arena_base + r.block + r.pl.off_drow,
+                                          (size_t)r.pl.sd[0].Np * 2, n * 2, n, cudaMemcpyDeviceToHost, S->poll_st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(S->poll_st);
-        if (dd) cudaFree(dd);
-        if (e != cudaSuccess) status = status_from_cuda(e);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            status = status_from_cuda(e);
+        } else {
+            for (size_t i = 1; i < n; ++i) memset(D_out + i * n, 0, i * 2);
+        }
     }
     if (r.bytes && r.n > 0 && r.state != 0) {
         std::lock_guard<std::mutex> lk(S->mu);
@@ -594,6 +956,7 @@ int fold_serve_stop(fold_ctx *ctx) {
     }
     if (S->th.joinable()) S->th.join();
     cudaSetDevice(ctx->device);
+    if (S->ring_on) ring_stop(S);
     cudaStreamSynchronize(S->st);
     cudaStreamSynchronize(S->poll_st);
     ctx->launches += S->launches;
@@ -604,6 +967,7 @@ int fold_serve_stop(fold_ctx *ctx) {
     cudaStreamDestroy(S->poll_st);
     cudaEventDestroy(S->ev0);
     cudaEventDestroy(S->ev1);
+    ring_teardown(S);
     delete S;
     ctx->serve = nullptr;
     return FOLD_OK;

@@ -23,6 +23,7 @@ FOLD_OPT_Q, FOLD_OPT_TILE, FOLD_OPT_LAUNCHES, FOLD_OPT_TEST_DROP_TASK = 5, 6, 7,
 FOLD_OPT_TIMING, FOLD_OPT_KERNEL_NS, FOLD_OPT_TRACE, FOLD_OPT_NEAR_CTAS, FOLD_OPT_COLUMNS = 9, 10, 11, 12, 13
 FOLD_OPT_BATCH_FLAT, FOLD_OPT_R_MEMO, FOLD_OPT_BATCH_GATHER = 14, 15, 16
 FOLD_OPT_COL_HELPERS = 17
+FOLD_OPT_SERVE_RING = 18
 FOLD_PAIRS_DEFAULT = 0x5A48   # AU UA CG GC GU UG
 FOLD_PAIRS_PAPER = 0x1248     # AU UA CG GC
 FOLD_MAX_N = 65535

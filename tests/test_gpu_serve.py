@@ -1,7 +1,8 @@
 """Serving (continuous batching) on the GPU: requests that arrive while
-others are in flight are admitted as memory frees up, share persistent
-launches with them, and every result equals the one the same sequence gives
-alone (exactly: the work is integer).  All calls go through the C-ABI."""
+others are in flight are admitted as memory frees up, share the persistent
+launch (the serving ring, or slice launches with FOLD_OPT_SERVE_RING = 0) with
+them, and every result equals the one the same sequence gives alone (exactly:
+the work is integer).  All calls go through the C-ABI."""
 import time
 
 import numpy as np
@@ -29,9 +30,11 @@ def _drain(ctx, tickets, timeout=120.0, want_D=None):
     return out
 
 
-def test_serve_mix_equals_alone():
+@pytest.mark.parametrize("ring", [1, 0])
+def test_serve_mix_equals_alone(ring):
     f = fold.Folder(q=8)
     try:
+        f.option(fold.FOLD_OPT_SERVE_RING, ring)
         kinds = ["uniform", "gc_rich", "structured"]
         lens = [0, 1, 2, 31, 32, 33, 100, 500, 1200, 64, 2500, 7, 300, 900]
         seqs = [synth.variant(kinds[k % 3], L, 900 + k) for k, L in enumerate(lens)]
@@ -89,15 +92,17 @@ def test_serve_lone_requests_fold_in_one_launch():
         st = fold.fold_serve_stats(f.ctx)
         assert st["solo"] == 5
         assert st["admitted"] == st["finished"] == len(seqs)
-        assert st["slices"] > st["solo"]   # the 9000-long one took several launches
+        assert st["slices"] > st["solo"]   # the 9000-long one took the ring launch (or slice launches)
     finally:
         fold.fold_serve_stop(f.ctx)
         f.close()
 
 
-def test_serve_wait_any_reports_each_finished_request_once():
+@pytest.mark.parametrize("ring", [1, 0])
+def test_serve_wait_any_reports_each_finished_request_once(ring):
     f = fold.Folder(q=8)
     try:
+        f.option(fold.FOLD_OPT_SERVE_RING, ring)
         fold.fold_serve_start(f.ctx, 8 << 30, 64)
         assert fold.fold_serve_wait_any(f.ctx, 20) is None   # nothing submitted: times out
         seqs = [synth.uniform(n, 70 + n) for n in (0, 5, 64, 400, 1500, 3000, 200)]
@@ -118,9 +123,11 @@ def test_serve_wait_any_reports_each_finished_request_once():
         f.close()
 
 
-def test_serve_budget_admission_and_tables():
+@pytest.mark.parametrize("ring", [1, 0])
+def test_serve_budget_admission_and_tables(ring):
     f = fold.Folder(q=8)
     try:
+        f.option(fold.FOLD_OPT_SERVE_RING, ring)
         one = f.workspace_bytes(800)
         # room for about three 800-base requests at a time
         fold.fold_serve_start(f.ctx, int(3.5 * one), 16)
@@ -174,6 +181,29 @@ def test_serve_warm_then_mixed_lengths():
         tickets = [fold.fold_serve_submit(f.ctx, s) for s in seqs]
         res = _drain(f.ctx, tickets)
         assert [res[t] for t in tickets] == [oracle.score(s) for s in seqs]
+    finally:
+        fold.fold_serve_stop(f.ctx)
+        f.close()
+
+
+def test_serve_ring_restarts_and_option_while_serving():
+    """The ring launch stops whenever nothing is in flight and starts again with the next requests;
+    bursts separated by idle gaps, each mixing short and long requests, all equal the oracle."""
+    f = fold.Folder(q=8)
+    try:
+        fold.fold_serve_start(f.ctx, 4 << 30, 64)
+        with pytest.raises(fold.FoldError) as ei:   # fixed while serving
+            f.option(fold.FOLD_OPT_SERVE_RING, 0)
+        assert ei.value.code == fold.FOLD_EAGAIN
+        for burst in range(3):
+            seqs = [synth.variant(["uniform", "structured"][k % 2], L, 7000 + 10 * burst + k)
+                    for k, L in enumerate([2500, 30, 600, 1, 1200, 90])]
+            tickets = [fold.fold_serve_submit(f.ctx, x) for x in seqs]
+            res = _drain(f.ctx, tickets)
+            assert [res[t] for t in tickets] == [oracle.score(x) if len(x) else 0 for x in seqs]
+            time.sleep(0.05)   # idle: the launch ends
+        st = fold.fold_serve_stats(f.ctx)
+        assert st["inflight"] == 0 and st["queued"] == 0
     finally:
         fold.fold_serve_stop(f.ctx)
         f.close()
