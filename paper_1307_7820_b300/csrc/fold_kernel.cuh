@@ -503,6 +503,37 @@ static __device__ __forceinline__ int hmax2(unsigned a) {
     return max((int)(short)(a & 0xffffu), (int)(short)(a >> 16));
 }
 
+// serving ring: lane 0 waits (bounded) until index idx is published or the host has stopped; the
+// verdict (1: no task for this claim) is broadcast.  A free function with scalar arguments, so that
+// neither the task claim nor the kernel parameters need an address.
+static __device__ __noinline__ int ring_wait(const int *tail, const int *stop, int *error, long long timeout_ns, int idx,
+                                             int lane) {
+    int st = 0;
+    if (lane == 0 && ld_acquire(tail) <= idx) {
+        const unsigned long long t0 = gtimer();
+        unsigned ns = 0;
+        for (;;) {
+            if (ld_acquire(tail) > idx) break;
+            if (ld_acquire(stop) != 0) {
+                if (ld_acquire(tail) > idx) break;
+                st = 1;
+                break;
+            }
+            if (*(volatile int *)error != 0) { st = 1; break; }
+            if ((long long)(gtimer() - t0) > timeout_ns) {
+                atomicCAS(error, 0, kErrTimeout);
+                st = 1;
+                break;
+            }
+            __nanosleep(ns);
+            ns = ns ? (ns < 1024 ? 2 * ns : 1024) : 64;
+        }
+    }
+    st = __shfl_sync(FULL, st, 0);
+    __syncwarp();
+    return st;
+}
+
 // The queue's next task for a worker: claimed while the worker finishes its current chunk, right
 // after the chunk's merges are issued, so that the claim's round trips (queue atomic, task load)
 // overlap the merges' completion.  The claim comes only the merge's duration early, so tasks still
@@ -516,7 +547,10 @@ struct NextTask {
     bool have;
     bool stopped;  // serving ring: the host stopped publishing and this claim has no task
     int pending;   // lane 0: the queue atomic's result, read by finish()
-    const FoldParams *P;
+    int ring_cap;  // serving ring (see FoldParams), 0 otherwise
+    const int *ring_tail, *ring_stop;
+    int *ring_progress, *error;
+    long long timeout_ns;
     // the queue atomic goes out here; its result is read by finish()
     __device__ __forceinline__ void start(int lane) {
         if (lane == 0) pending = atomicAdd(qhead, 1);
@@ -526,41 +560,15 @@ struct NextTask {
         idx = i;
         // serving ring: the task is fetched by fetch() once the current task is complete (a chunk
         // claims its successor before it counts itself done, and the successor may not be published)
-        tk = (P->ring_cap == 0 && i < qlimit) ? tasks[i] : make_int4(0, 0, 0, 0);
+        tk = (ring_cap == 0 && i < qlimit) ? tasks[i] : make_int4(0, 0, 0, 0);
         have = true;
     }
     // serving ring: wait until the claimed task is published (or the host stopped), then load it
     __device__ __forceinline__ void fetch(int lane) {
-        if (P->ring_cap == 0) return;
-        ring_wait(lane);
-        tk = stopped ? make_int4(0, 0, 0, 0) : __ldcg(tasks + (idx % P->ring_cap));
-        if (lane == 0 && (idx & 255) == 0) *(volatile int *)P->ring_progress = idx;
-    }
-    // serving ring: wait (bounded) until the claimed index is published or the host has stopped
-    __device__ __noinline__ void ring_wait(int lane) {
-        int st = 0;
-        if (lane == 0 && ld_acquire(P->ring_tail) <= idx) {
-            const unsigned long long t0 = gtimer();
-            unsigned ns = 0;
-            for (;;) {
-                if (ld_acquire(P->ring_tail) > idx) break;
-                if (ld_acquire(P->ring_stop) != 0) {
-                    if (ld_acquire(P->ring_tail) > idx) break;
-                    st = 1;
-                    break;
-                }
-                if (*(volatile int *)P->error != 0) { st = 1; break; }
-                if ((long long)(gtimer() - t0) > P->timeout_ns) {
-                    atomicCAS(P->error, 0, kErrTimeout);
-                    st = 1;
-                    break;
-                }
-                __nanosleep(ns);
-                ns = ns ? (ns < 1024 ? 2 * ns : 1024) : 64;
-            }
-        }
-        stopped = __shfl_sync(FULL, st, 0) != 0;
-        __syncwarp();
+        if (ring_cap == 0) return;
+        stopped = ring_wait(ring_tail, ring_stop, error, timeout_ns, idx, lane) != 0;
+        tk = stopped ? make_int4(0, 0, 0, 0) : __ldcg(tasks + (idx % ring_cap));
+        if (lane == 0 && (idx & 255) == 0) *(volatile int *)ring_progress = idx;
     }
     __device__ __forceinline__ void claim(int lane) {
         start(lane);
@@ -1780,7 +1788,12 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
     nt.tasks = P.tasks;
     nt.have = false;
     nt.stopped = false;
-    nt.P = &P;
+    nt.ring_cap = P.ring_cap;
+    nt.ring_tail = P.ring_tail;
+    nt.ring_stop = P.ring_stop;
+    nt.ring_progress = P.ring_progress;
+    nt.error = P.error;
+    nt.timeout_ns = P.timeout_ns;
     int err = 0;   // the error word as read when the previous task started
     for (;;) {
         if (!nt.have) nt.claim(lane);
