@@ -51,6 +51,7 @@ constexpr size_t kLaunchBytes0 = size_t(16) << 20;   // initial launch-list buff
 constexpr int kRingCap = 1 << 22;    // serving ring: tasks (64 MiB)
 constexpr long long kRingAhead = 8192;   // tasks published ahead of the claims the launch reported
 constexpr int kResultPending = INT32_MIN;
+constexpr size_t kSoloListBytes = size_t(256) << 20;   // device copies of lone requests' task lists
 
 struct Request {
     uint64_t ticket = 0;
@@ -125,6 +126,18 @@ struct ServeState {
     // launch buffers
     DevBuf d_launch;                 // control | results | SeqDesc | tasks
     HostBuf h_launch;
+    // a lone request's task list (in the layout of its work split) kept on the device per (tiles per
+    // side, chunk size), so that a size seen before launches without building or copying its list;
+    // least recently used dropped past kSoloListBytes
+    struct SoloList {
+        void *dev = nullptr;
+        size_t bytes = 0;
+        int ntasks = 0, nnear = 0;
+        unsigned long long used = 0;
+    };
+    std::map<std::pair<int, int>, SoloList> solo_lists;
+    size_t solo_list_bytes = 0;
+    unsigned long long solo_clock = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     unsigned long long launches = 0;
     fold_serve_stats stats{};        // guarded by mu
@@ -539,36 +552,66 @@ static void serve_loop(ServeState *S) {
             const FoldOpts o;   // automatic work split, whatever the caller's options
             const SplitPlan sp = plan_split(ctx, o, r.NT, grid_for(ctx), true);
             const size_t nt = sc.tasks.size();
-            // launch buffers: SeqDesc | result | tasks; with tile-only CTAs the list is split into
-            // [tile tasks | chunks], each in the template's order (its tiles are by diagonal, as
-            // column mode reads them): both parts are whole ranges of every step
-            const size_t o_res = 256, o_tasks = 512, need = al256(o_tasks + sizeof(int4) * nt);
-            if (ensure_buf(S->d_launch, grown(S->d_launch.bytes, need)) == FOLD_OK &&
+            // the list on the device: with tile-only CTAs split into [tile tasks | chunks], each in
+            // the template's order (its tiles are by diagonal, as column mode reads them): both
+            // parts are whole ranges of every step
+            const auto key = std::make_pair(r.NT, ctx->kc_override > 0 ? ctx->kc_override : kc_auto(r.NT));
+            auto li = S->solo_lists.find(key);
+            if (li == S->solo_lists.end() && ensure_host(S->h_launch, grown(S->h_launch.bytes, al256(sizeof(int4) * nt))) == FOLD_OK) {
+                // drop the least recently used lists to make room (the server is idle: nothing reads them)
+                const size_t bytes = al256(sizeof(int4) * std::max<size_t>(nt, 1));
+                while (!S->solo_lists.empty() && S->solo_list_bytes + bytes > kSoloListBytes) {
+                    auto victim = S->solo_lists.begin();
+                    for (auto it = S->solo_lists.begin(); it != S->solo_lists.end(); ++it)
+                        if (it->second.used < victim->second.used) victim = it;
+                    cudaFree(victim->second.dev);
+                    S->solo_list_bytes -= victim->second.bytes;
+                    S->solo_lists.erase(victim);
+                }
+                ServeState::SoloList L;
+                if (cudaMalloc(&L.dev, bytes) == cudaSuccess) {
+                    int4 *dst = reinterpret_cast<int4 *>(S->h_launch.ptr);
+                    int nnear = 0;
+                    if (sp.near_ctas > 0) {
+                        for (int t = 0; t < r.NT; ++t) {
+                            const int a = sc.near_begin[t], b = sc.chunk_begin[t];
+                            memcpy(dst, sc.tasks.data() + a, sizeof(int4) * (size_t)(b - a));
+                            dst += b - a;
+                            nnear += b - a;
+                        }
+                        for (int t = 0; t < r.NT; ++t) {
+                            const int a = sc.chunk_begin[t], b = sc.near_begin[t + 1];
+                            memcpy(dst, sc.tasks.data() + a, sizeof(int4) * (size_t)(b - a));
+                            dst += b - a;
+                        }
+                    } else {
+                        memcpy(dst, sc.tasks.data(), sizeof(int4) * nt);
+                    }
+                    L.bytes = bytes;
+                    L.ntasks = (int)nt;
+                    L.nnear = nnear;
+                    e = cudaMemcpy(L.dev, S->h_launch.ptr, sizeof(int4) * nt, cudaMemcpyHostToDevice);
+                    if (e == cudaSuccess) {
+                        li = S->solo_lists.emplace(key, L).first;
+                        S->solo_list_bytes += bytes;
+                    } else {
+                        cudaFree(L.dev);
+                    }
+                } else {
+                    cudaGetLastError();
+                }
+            }
+            // launch buffers: SeqDesc | result
+            const size_t o_res = 256, need = 512;
+            if (e == cudaSuccess && li != S->solo_lists.end() && ensure_buf(S->d_launch, grown(S->d_launch.bytes, need)) == FOLD_OK &&
                 ensure_host(S->h_launch, grown(S->h_launch.bytes, need)) == FOLD_OK) {
+                li->second.used = ++S->solo_clock;
+                const int nnear = li->second.nnear;
                 uint8_t *h = reinterpret_cast<uint8_t *>(S->h_launch.ptr);
                 uint8_t *d = reinterpret_cast<uint8_t *>(S->d_launch.ptr);
                 memcpy(h, &r.pl.sd[0], sizeof(SeqDesc));
-                int4 *dst = reinterpret_cast<int4 *>(h + o_tasks);
-                int nnear = 0;
-                if (sp.near_ctas > 0) {
-                    for (int t = 0; t < r.NT; ++t) {
-                        const int a = sc.near_begin[t], b = sc.chunk_begin[t];
-                        memcpy(dst, sc.tasks.data() + a, sizeof(int4) * (size_t)(b - a));
-                        dst += b - a;
-                        nnear += b - a;
-                    }
-                    for (int t = 0; t < r.NT; ++t) {
-                        const int a = sc.chunk_begin[t], b = sc.near_begin[t + 1];
-                        memcpy(dst, sc.tasks.data() + a, sizeof(int4) * (size_t)(b - a));
-                        dst += b - a;
-                    }
-                } else {
-                    memcpy(dst, sc.tasks.data(), sizeof(int4) * nt);
-                }
                 if (e == cudaSuccess) e = cudaMemcpyAsync(d, h, sizeof(SeqDesc), cudaMemcpyHostToDevice, S->st);
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(d + o_tasks, h + o_tasks, sizeof(int4) * nt, cudaMemcpyHostToDevice, S->st);
-                FoldParams p = make_params(ctx, r.pl, S->arena_base + r.block, reinterpret_cast<const int4 *>(d + o_tasks),
+                FoldParams p = make_params(ctx, r.pl, S->arena_base + r.block, reinterpret_cast<const int4 *>(li->second.dev),
                                            (int)nt, reinterpret_cast<const SeqDesc *>(d));
                 if (sp.near_ctas > 0) {
                     p.col_mode = sp.col_mode;
@@ -962,6 +1005,7 @@ int fold_serve_stop(fold_ctx *ctx) {
     ctx->launches += S->launches;
     if (S->d_launch.ptr) cudaFree(S->d_launch.ptr);
     if (S->h_launch.ptr) cudaFreeHost(S->h_launch.ptr);
+    for (auto &kv : S->solo_lists) cudaFree(kv.second.dev);
     cudaFree(S->arena_base);
     cudaStreamDestroy(S->st);
     cudaStreamDestroy(S->poll_st);
