@@ -418,8 +418,13 @@ int fold_serve_wait_any(fold_ctx *ctx, int32_t timeout_ms, uint64_t *ticket);
  * they depend only on the length and are otherwise built when a length is
  * first seen, adding that time (up to about 10 ms at n = 8000) to the first
  * request of each size.  Lists are kept for the life of the process (up to
- * 512 MiB, least recently used dropped first).  FOLD_EINVAL if ctx is NULL or
- * max_n is outside [0, 65535]. */
+ * 512 MiB, least recently used dropped first).  It also copies to the device,
+ * for lengths up to 8192, the list a request arriving to an idle server folds
+ * with (about 240 MiB for all of them, kept with the context; otherwise made
+ * at the first lone request of each size, about 1 ms at n = 8000); this
+ * allocates device memory and may wait for work already on the device.
+ * FOLD_EINVAL if ctx is NULL or max_n is outside [0, 65535]; FOLD_ECUDA if a
+ * device copy failed. */
 int fold_serve_warm(fold_ctx *ctx, int32_t max_n);
 
 /* Counters of the serving loop since fold_serve_start (for monitoring and

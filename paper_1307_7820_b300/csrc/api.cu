@@ -680,6 +680,7 @@ void fold_destroy(fold_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (auto &kv : ctx->sched_cache) cudaFree(kv.second.dev);
+    for (auto &kv : ctx->solo_lists) cudaFree(kv.second.dev);
     if (ctx->d_rcanon) cudaFree(ctx->d_rcanon);
     if (ctx->d_rpacked_buf) cudaFree(ctx->d_rpacked_buf);
     if (ctx->ws.ptr) cudaFree(ctx->ws.ptr);

@@ -7,6 +7,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "fold_common.h"
@@ -16,6 +17,14 @@ namespace fold {
 
 struct DevBuf { void *ptr = nullptr; size_t bytes = 0; };
 struct HostBuf { void *ptr = nullptr; size_t bytes = 0; };
+
+// A lone serving request's task list on the device (see fold_ctx::solo_lists).
+struct SoloList {
+    void *dev = nullptr;
+    size_t bytes = 0;
+    int ntasks = 0, nnear = 0;
+    unsigned long long used = 0;
+};
 
 struct CachedSched {
     void *dev = nullptr;
@@ -98,6 +107,14 @@ struct fold_ctx {
     fold::DevBuf trace_buf;
     int trace_count = 0;
     fold::ServeState *serve = nullptr;
+    // serving: the task lists of lone requests (folded with the single fold's work split) on the
+    // device per (tiles per side, chunk size, split into tile and chunk queues), built at first use
+    // or ahead by fold_serve_warm, kept for the context's life (least recently used dropped past
+    // 256 MiB)
+    std::map<std::tuple<int, int, bool>, fold::SoloList> solo_lists;   // guarded by solo_mu
+    std::mutex solo_mu;
+    size_t solo_list_bytes = 0;
+    unsigned long long solo_clock = 0;
 };
 
 namespace fold {

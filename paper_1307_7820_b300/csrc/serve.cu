@@ -126,18 +126,7 @@ struct ServeState {
     // launch buffers
     DevBuf d_launch;                 // control | results | SeqDesc | tasks
     HostBuf h_launch;
-    // a lone request's task list (in the layout of its work split) kept on the device per (tiles per
-    // side, chunk size), so that a size seen before launches without building or copying its list;
-    // least recently used dropped past kSoloListBytes
-    struct SoloList {
-        void *dev = nullptr;
-        size_t bytes = 0;
-        int ntasks = 0, nnear = 0;
-        unsigned long long used = 0;
-    };
-    std::map<std::pair<int, int>, SoloList> solo_lists;
-    size_t solo_list_bytes = 0;
-    unsigned long long solo_clock = 0;
+
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     unsigned long long launches = 0;
     fold_serve_stats stats{};        // guarded by mu
@@ -292,6 +281,68 @@ static cudaError_t ring_start(ServeState *S) {
         S->stats.slices++;
     }
     return e;
+}
+
+// The device copy of a lone request's task list (template sc of NT tiles per side; with split, as
+// [tile tasks | chunk tasks], each in the template's order -- its tiles by diagonal, as column mode
+// reads them -- both parts whole ranges of every step), from the context's cache or built now
+// through `staging` on stream st.  *out receives the entry (dev null if it could not be made).
+// Only an idle server or fold_serve_warm builds: eviction frees device memory.
+static cudaError_t solo_list(fold_ctx *ctx, int NT, const SeqTemplate &sc, bool split, HostBuf *staging,
+                             cudaStream_t st, SoloList *out) {
+    *out = SoloList();
+    const auto key = std::make_tuple(NT, ctx->kc_override > 0 ? ctx->kc_override : kc_auto(NT), split);
+    std::lock_guard<std::mutex> lk(ctx->solo_mu);
+    auto it = ctx->solo_lists.find(key);
+    if (it != ctx->solo_lists.end()) {
+        it->second.used = ++ctx->solo_clock;
+        *out = it->second;
+        return cudaSuccess;
+    }
+    const size_t nt = sc.tasks.size(), bytes = al256(sizeof(int4) * std::max<size_t>(nt, 1));
+    if (ensure_host(*staging, grown(staging->bytes, bytes)) != FOLD_OK) return cudaSuccess;
+    while (!ctx->solo_lists.empty() && ctx->solo_list_bytes + bytes > kSoloListBytes) {
+        auto victim = ctx->solo_lists.begin();
+        for (auto v = ctx->solo_lists.begin(); v != ctx->solo_lists.end(); ++v)
+            if (v->second.used < victim->second.used) victim = v;
+        cudaFree(victim->second.dev);
+        ctx->solo_list_bytes -= victim->second.bytes;
+        ctx->solo_lists.erase(victim);
+    }
+    SoloList L;
+    if (cudaMalloc(&L.dev, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return cudaSuccess;
+    }
+    int4 *dst = reinterpret_cast<int4 *>(staging->ptr);
+    if (split) {
+        for (int t = 0; t < NT; ++t) {
+            const int a = sc.near_begin[t], b = sc.chunk_begin[t];
+            memcpy(dst, sc.tasks.data() + a, sizeof(int4) * (size_t)(b - a));
+            dst += b - a;
+            L.nnear += b - a;
+        }
+        for (int t = 0; t < NT; ++t) {
+            const int a = sc.chunk_begin[t], b = sc.near_begin[t + 1];
+            memcpy(dst, sc.tasks.data() + a, sizeof(int4) * (size_t)(b - a));
+            dst += b - a;
+        }
+    } else {
+        memcpy(dst, sc.tasks.data(), sizeof(int4) * nt);
+    }
+    L.bytes = bytes;
+    L.ntasks = (int)nt;
+    cudaError_t e = cudaMemcpyAsync(L.dev, staging->ptr, sizeof(int4) * nt, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the staging is reused
+    if (e != cudaSuccess) {
+        cudaFree(L.dev);
+        return e;
+    }
+    L.used = ++ctx->solo_clock;
+    ctx->solo_lists.emplace(key, L);
+    ctx->solo_list_bytes += bytes;
+    *out = L;
+    return cudaSuccess;
 }
 
 // Copies `bytes` from pinned staging (or zeros) to the device on the copy stream, in pieces the
@@ -552,66 +603,19 @@ static void serve_loop(ServeState *S) {
             const FoldOpts o;   // automatic work split, whatever the caller's options
             const SplitPlan sp = plan_split(ctx, o, r.NT, grid_for(ctx), true);
             const size_t nt = sc.tasks.size();
-            // the list on the device: with tile-only CTAs split into [tile tasks | chunks], each in
-            // the template's order (its tiles are by diagonal, as column mode reads them): both
-            // parts are whole ranges of every step
-            const auto key = std::make_pair(r.NT, ctx->kc_override > 0 ? ctx->kc_override : kc_auto(r.NT));
-            auto li = S->solo_lists.find(key);
-            if (li == S->solo_lists.end() && ensure_host(S->h_launch, grown(S->h_launch.bytes, al256(sizeof(int4) * nt))) == FOLD_OK) {
-                // drop the least recently used lists to make room (the server is idle: nothing reads them)
-                const size_t bytes = al256(sizeof(int4) * std::max<size_t>(nt, 1));
-                while (!S->solo_lists.empty() && S->solo_list_bytes + bytes > kSoloListBytes) {
-                    auto victim = S->solo_lists.begin();
-                    for (auto it = S->solo_lists.begin(); it != S->solo_lists.end(); ++it)
-                        if (it->second.used < victim->second.used) victim = it;
-                    cudaFree(victim->second.dev);
-                    S->solo_list_bytes -= victim->second.bytes;
-                    S->solo_lists.erase(victim);
-                }
-                ServeState::SoloList L;
-                if (cudaMalloc(&L.dev, bytes) == cudaSuccess) {
-                    int4 *dst = reinterpret_cast<int4 *>(S->h_launch.ptr);
-                    int nnear = 0;
-                    if (sp.near_ctas > 0) {
-                        for (int t = 0; t < r.NT; ++t) {
-                            const int a = sc.near_begin[t], b = sc.chunk_begin[t];
-                            memcpy(dst, sc.tasks.data() + a, sizeof(int4) * (size_t)(b - a));
-                            dst += b - a;
-                            nnear += b - a;
-                        }
-                        for (int t = 0; t < r.NT; ++t) {
-                            const int a = sc.chunk_begin[t], b = sc.near_begin[t + 1];
-                            memcpy(dst, sc.tasks.data() + a, sizeof(int4) * (size_t)(b - a));
-                            dst += b - a;
-                        }
-                    } else {
-                        memcpy(dst, sc.tasks.data(), sizeof(int4) * nt);
-                    }
-                    L.bytes = bytes;
-                    L.ntasks = (int)nt;
-                    L.nnear = nnear;
-                    e = cudaMemcpy(L.dev, S->h_launch.ptr, sizeof(int4) * nt, cudaMemcpyHostToDevice);
-                    if (e == cudaSuccess) {
-                        li = S->solo_lists.emplace(key, L).first;
-                        S->solo_list_bytes += bytes;
-                    } else {
-                        cudaFree(L.dev);
-                    }
-                } else {
-                    cudaGetLastError();
-                }
-            }
+            // the list on the device, built at first use of the size (or by fold_serve_warm)
+            SoloList L;
+            e = solo_list(ctx, r.NT, sc, sp.near_ctas > 0, &S->h_launch, S->st, &L);
             // launch buffers: SeqDesc | result
             const size_t o_res = 256, need = 512;
-            if (e == cudaSuccess && li != S->solo_lists.end() && ensure_buf(S->d_launch, grown(S->d_launch.bytes, need)) == FOLD_OK &&
+            if (e == cudaSuccess && L.dev && ensure_buf(S->d_launch, grown(S->d_launch.bytes, need)) == FOLD_OK &&
                 ensure_host(S->h_launch, grown(S->h_launch.bytes, need)) == FOLD_OK) {
-                li->second.used = ++S->solo_clock;
-                const int nnear = li->second.nnear;
+                const int nnear = L.nnear;
                 uint8_t *h = reinterpret_cast<uint8_t *>(S->h_launch.ptr);
                 uint8_t *d = reinterpret_cast<uint8_t *>(S->d_launch.ptr);
                 memcpy(h, &r.pl.sd[0], sizeof(SeqDesc));
                 if (e == cudaSuccess) e = cudaMemcpyAsync(d, h, sizeof(SeqDesc), cudaMemcpyHostToDevice, S->st);
-                FoldParams p = make_params(ctx, r.pl, S->arena_base + r.block, reinterpret_cast<const int4 *>(li->second.dev),
+                FoldParams p = make_params(ctx, r.pl, S->arena_base + r.block, reinterpret_cast<const int4 *>(L.dev),
                                            (int)nt, reinterpret_cast<const SeqDesc *>(d));
                 if (sp.near_ctas > 0) {
                     p.col_mode = sp.col_mode;
@@ -975,7 +979,24 @@ int fold_serve_warm(fold_ctx *ctx, int32_t max_n) {
     for (int k = 1; k < nth; ++k) th.emplace_back(work);
     work();
     for (auto &x : th) x.join();
-    return FOLD_OK;
+    // the device copies of the lists a lone request launches with (lengths up to kSoloMaxN), in the
+    // layout of the automatic work split, through a stream that waits on no other
+    int ns = std::min(max_n, kSoloMaxN);
+    const int NTsolo = make_plan(&ns, 1, ctx->q, ctx->method).NTs[0];
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return FOLD_ECUDA;
+    HostBuf staging;
+    cudaError_t e = cudaSuccess;
+    for (int NT = 2; NT <= NTsolo && e == cudaSuccess; ++NT) {
+        const SplitPlan sp = plan_split(ctx, FoldOpts(), NT, grid_for(ctx), true);
+        SoloList L;
+        e = solo_list(ctx, NT, *seq_template(NT, kco > 0 ? kco : kc_auto(NT), strip, true), sp.near_ctas > 0, &staging,
+                      st, &L);
+    }
+    cudaStreamDestroy(st);
+    if (staging.ptr) cudaFreeHost(staging.ptr);
+    return e == cudaSuccess ? FOLD_OK : FOLD_ECUDA;
 }
 
 int fold_serve_stats_get(fold_ctx *ctx, fold_serve_stats *out) {
@@ -1005,7 +1026,6 @@ int fold_serve_stop(fold_ctx *ctx) {
     ctx->launches += S->launches;
     if (S->d_launch.ptr) cudaFree(S->d_launch.ptr);
     if (S->h_launch.ptr) cudaFreeHost(S->h_launch.ptr);
-    for (auto &kv : S->solo_lists) cudaFree(kv.second.dev);
     cudaFree(S->arena_base);
     cudaStreamDestroy(S->st);
     cudaStreamDestroy(S->poll_st);
