@@ -109,10 +109,11 @@ enum fold_option {
                                  segment list is copied per call; default); 0 = built on the host and
                                  copied whole.  Results are identical. */
     FOLD_OPT_COL_HELPERS = 17, /* single folds in column mode, two-vector: -1 = automatic (on where the
-                                  layout has at most 4 columns per tile CTA), 1 = on, 0 = off.  On, warp
-                                  w + 4 of each tile CTA helps column warp w: it loads each tile's inputs,
-                                  does its late middle blocks' lookups and the chunk merge, and publishes
-                                  each finished tile, so the column warp only computes rows */
+                                  layout has at most 4 columns per tile CTA and the fold at most 150
+                                  tiles per side), 1 = on, 0 = off.  On, warp w + 4 of each tile CTA
+                                  helps column warp w: it loads each next tile's inputs and does its
+                                  late middle blocks' lookups and the chunk merge while the column warp
+                                  computes rows.  Results are identical. */
     FOLD_OPT_SERVE_RING = 18   /* serving: 1 (default) = requests in flight are folded by one persistent
                                   launch fed while it runs (a task ring the serving thread fills round
                                   by round); 0 = repeated launches, each a slice of tile diagonals of
