@@ -287,9 +287,11 @@ static cudaError_t ring_start(ServeState *S) {
 // [tile tasks | chunk tasks], each in the template's order -- its tiles by diagonal, as column mode
 // reads them -- both parts whole ranges of every step), from the context's cache or built now
 // through `staging` on stream st.  *out receives the entry (dev null if it could not be made).
-// Only an idle server or fold_serve_warm builds: eviction frees device memory.
+// Making room drops the least recently used lists, which only the serving thread may do (may_evict),
+// and only while no launch is in flight: another thread could free a list between its lookup and its
+// launch.
 static cudaError_t solo_list(fold_ctx *ctx, int NT, const SeqTemplate &sc, bool split, HostBuf *staging,
-                             cudaStream_t st, SoloList *out) {
+                             cudaStream_t st, bool may_evict, SoloList *out) {
     *out = SoloList();
     const auto key = std::make_tuple(NT, ctx->kc_override > 0 ? ctx->kc_override : kc_auto(NT), split);
     std::lock_guard<std::mutex> lk(ctx->solo_mu);
@@ -300,6 +302,7 @@ static cudaError_t solo_list(fold_ctx *ctx, int NT, const SeqTemplate &sc, bool 
         return cudaSuccess;
     }
     const size_t nt = sc.tasks.size(), bytes = al256(sizeof(int4) * std::max<size_t>(nt, 1));
+    if (!may_evict && ctx->solo_list_bytes + bytes > kSoloListBytes) return cudaSuccess;
     if (ensure_host(*staging, grown(staging->bytes, bytes)) != FOLD_OK) return cudaSuccess;
     while (!ctx->solo_lists.empty() && ctx->solo_list_bytes + bytes > kSoloListBytes) {
         auto victim = ctx->solo_lists.begin();
@@ -605,7 +608,7 @@ static void serve_loop(ServeState *S) {
             const size_t nt = sc.tasks.size();
             // the list on the device, built at first use of the size (or by fold_serve_warm)
             SoloList L;
-            e = solo_list(ctx, r.NT, sc, sp.near_ctas > 0, &S->h_launch, S->st, &L);
+            e = solo_list(ctx, r.NT, sc, sp.near_ctas > 0, &S->h_launch, S->st, true, &L);
             // launch buffers: SeqDesc | result
             const size_t o_res = 256, need = 512;
             if (e == cudaSuccess && L.dev && ensure_buf(S->d_launch, grown(S->d_launch.bytes, need)) == FOLD_OK &&
@@ -992,7 +995,7 @@ int fold_serve_warm(fold_ctx *ctx, int32_t max_n) {
         const SplitPlan sp = plan_split(ctx, FoldOpts(), NT, grid_for(ctx), true);
         SoloList L;
         e = solo_list(ctx, NT, *seq_template(NT, kco > 0 ? kco : kc_auto(NT), strip, true), sp.near_ctas > 0, &staging,
-                      st, &L);
+                      st, false, &L);
     }
     cudaStreamDestroy(st);
     if (staging.ptr) cudaFreeHost(staging.ptr);
