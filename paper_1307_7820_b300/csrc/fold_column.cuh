@@ -80,6 +80,55 @@ struct ColMain {
     bool consumer;     // the next column's warps run in this CTA
 };
 
+// Main warp, before a tile: waits (bounded) until the helper has published the tile's prep
+// (*prep >= target) and, with nfar > 0, until the tile's chunk counter reaches nfar, starting the
+// copy of the P slot (nints ints) into dst as soon as it does; the counter is polled every fourth
+// round, so the prep is seen within a few shared-memory round trips.  Returns false if a wait gave
+// up (no copy is then left in flight).
+static __device__ __noinline__ bool wait_prep_and_slot(const int *prep, int target, const int *cnt, int nfar,
+                                                       const int *slot, int *dst, int nints, int *error,
+                                                       long long timeout_ns, int lane) {
+    bool have_p = nfar <= 0, have_prep = false;
+    const unsigned long long t0 = gtimer();
+    for (unsigned it = 0;; ++it) {
+        if (!have_p && (it & 3u) == 0) {
+            int v = 0;
+            if (lane == 0) v = ld_acquire(cnt);
+            if (__shfl_sync(FULL, v, 0) >= nfar) {
+                __syncwarp();   // every lane's copy after lane 0's acquire
+                for (int q = lane; q < nints / 4; q += 32)
+                    cp_async16(reinterpret_cast<int4 *>(dst) + q, reinterpret_cast<const int4 *>(slot) + q);
+                cp_async_commit();
+                have_p = true;
+            }
+        }
+        if (!have_prep) {
+            int v = 0;
+            if (lane == 0) v = ld_acquire_cta(prep);
+            have_prep = __shfl_sync(FULL, v, 0) >= target;
+        }
+        if (have_p && have_prep) break;
+        if ((it & 31u) == 31u) {
+            int bad = 0;
+            if (lane == 0) {
+                if (*(volatile int *)error != 0) bad = 1;
+                else if ((long long)(gtimer() - t0) > timeout_ns) {
+                    atomicCAS(error, 0, kErrTimeout);
+                    bad = 1;
+                }
+            }
+            if (__shfl_sync(FULL, bad, 0)) {
+                cp_async_wait_all();
+                __syncwarp();
+                return false;
+            }
+        }
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    return true;
+}
+
 // Tile (I,J) = the column's k-th tile, t = J - I = k.  Returns false if a wait gave up.
 template <int Q, bool MEMO>
 __device__ __forceinline__ bool col_main_tile(const FoldParams &P, const SeqDesc &sd, int I, int J, int k, int nfar,
@@ -98,7 +147,13 @@ __device__ __forceinline__ bool col_main_tile(const FoldParams &P, const SeqDesc
     int16_t(*tile)[33] = (k & 1) ? ws.tile1 : ws.tile;
     // the next column's helper must have read this column's tile k-2 before its buffer is rewritten
     if (cs.consumer && k >= 2 && !wait_smem_geq(&ha.consumed, k - 1, P.error, P.timeout_ns, lane)) return false;
-    if (!wait_smem_geq(&ha.prep_ready, k + 1, P.error, P.timeout_ns, lane)) return false;
+    // the helper's prep, and the chunks' partial maximum of the middle blocks I+2 .. J-2 (the P
+    // slot), copied into shared memory as soon as the tile's chunk counter is complete
+    const int *pslot = P.pring + sd.p_off + ((size_t)(t % kRing) * NT + I) * (T * T);
+    constexpr bool PB = WS::PB;   // else the helper merges the slot into the prep
+    if (!wait_prep_and_slot(&ha.prep_ready, k + 1, P.cnt + sd.cnt_off + I * NT + J, PB ? nfar : 0, pslot, ws.pbuf,
+                            PB ? T * T : 0, P.error, P.timeout_ns, lane))
+        return false;
     if (tr) tr[0] = (long long)gtimer();
     const ColPrep<Q> &pp = ha.prep[k & 1];
     const unsigned pbits = pp.pbits[lane];
@@ -184,6 +239,7 @@ __device__ __forceinline__ bool col_main_tile(const FoldParams &P, const SeqDesc
         // maximum, the residual splits in the window of rows below, the full groups of tile column I
         auto old_terms = [&](int rr) -> int {
             int best = (int)pp.pm[rr][c];
+            if (PB && nfar > 0) best = max(best, ws.pbuf[min(rr * T + c, T * T - 1)]);
             unsigned ra = 0u, rb = 0u;
 #pragma unroll
             for (int k4 = 0; k4 < WS::NWPA / 4; ++k4) {
@@ -414,10 +470,12 @@ __device__ __forceinline__ bool col_help_prep(const FoldParams &P, const SeqDesc
         for (int gl = 0; gl < G; ++gl) hs.lcb0[gl] = valid ? ha.lcb0[c][gl] : 0u;
         hs.have_lcb0 = true;
     }
-    // C: the chunks' partial maximum of middle blocks I+2 .. J-2 (P slot), merged as soon as the
-    // tile's chunk counter is seen complete (polled between the steps below, awaited at the end)
+    // C, only where the main warp keeps no shared-memory copy of the P slot (WarpScratch::PB false):
+    // the chunks' partial maximum of middle blocks I+2 .. J-2, merged as soon as the tile's chunk
+    // counter is seen complete (polled between the steps below, awaited at the end).  Elsewhere the
+    // main warp copies the slot itself while it waits for the prep.
     const int idx = t * NT - t * (t - 1) / 2 + I;   // tile (I,J) among the diagonal-ordered tile tasks
-    const int nfar = t >= 1 ? P.tasks[idx].z : 0;
+    const int nfar = (!WS::PB && t >= 1) ? P.tasks[idx].z : 0;
     bool p_done = nfar == 0;
     const int *cntp = P.cnt + sd.cnt_off + I * NT + J;
     auto merge_p = [&]() {
