@@ -114,11 +114,15 @@ enum fold_option {
                                   helps column warp w: it loads each next tile's inputs and does its
                                   late middle blocks' lookups and the chunk merge while the column warp
                                   computes rows.  Results are identical. */
-    FOLD_OPT_SERVE_RING = 18   /* serving: 1 (default) = requests in flight are folded by one persistent
+    FOLD_OPT_SERVE_RING = 18,  /* serving: 1 (default) = requests in flight are folded by one persistent
                                   launch fed while it runs (a task ring the serving thread fills round
                                   by round); 0 = repeated launches, each a slice of tile diagonals of
                                   every request.  Set before fold_serve_start (FOLD_EAGAIN while
                                   serving).  Results are identical. */
+    FOLD_OPT_COL_JOIN = 19     /* single folds in column mode: -1 = automatic (on without column
+                                  helpers), 1 = on, 0 = off.  On, the warps of a tile CTA whose tile
+                                  columns are all finished take chunk tasks beside the chunk CTAs.
+                                  Results are identical. */
 };
 
 /* One record per task of the last traced persistent launch. */

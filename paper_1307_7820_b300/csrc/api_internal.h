@@ -78,6 +78,7 @@ struct fold_ctx {
     int near_ctas_opt = -1;    // -1 automatic, 0 one shared queue, k > 0 k tile-only CTAs
     int columns_opt = -1;      // -1 automatic, 0 off, v >= 1 column mode with v columns per tile CTA
     int col_helpers_opt = -1;  // FOLD_OPT_COL_HELPERS: -1 automatic, 0 off, 1 on (column mode, two-vector)
+    int col_join_opt = -1;     // FOLD_OPT_COL_JOIN: -1 automatic (without helpers), 0 off, 1 on
     int serve_ring = 1;        // FOLD_OPT_SERVE_RING: serving through one persistent launch fed while it runs
     int batch_flat_opt = -1;   // fold_batch chunks: -1 / 1 kc blocks each, 0 geometric sizes
     int batch_gather = 1;      // FOLD_OPT_BATCH_GATHER: fold_batch's list gathered on the device
@@ -130,6 +131,7 @@ struct SplitPlan {
     int col_mode = 0;    // 1: column mode
     int cpc = kWarpsPerCta;   // columns per tile CTA in column mode
     int helpers = 0;     // 1: column mode with a helper warp per column (cpc <= kWarpsPerCta / 2)
+    int join = 0;        // 1: column mode, a tile CTA's warps take chunks once its columns are done
 };
 SplitPlan plan_split(fold_ctx *ctx, const FoldOpts &o, int NT, int grid, bool layout_ok);
 FoldOpts single_opts(const fold_ctx *ctx, int n);

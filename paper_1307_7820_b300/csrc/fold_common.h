@@ -81,6 +81,8 @@ struct FoldParams {
     // (cols_per_cta <= kWarpsPerCta/2): it prepares each tile's inputs and publishes each finished
     // tile, so the column warp only computes rows (see fold_column.cuh)
     int col_helpers;
+    // column mode: the warps of a tile CTA whose columns are all finished take chunk tasks
+    int col_join;
     // two-vector, q <= 9: launch the kernel instantiation in which R starts empty in each CTA and a
     // row R[h][*] is tabulated against every column vector the first time a warp of the CTA stages a
     // feature with horizontal vector h (Section 3.2's partially memoised variant); 0: the one that

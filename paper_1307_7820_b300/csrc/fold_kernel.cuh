@@ -1684,6 +1684,15 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
     __syncthreads();
     const bool split = P.near_ctas > 0;
     const bool far_role = split && (int)blockIdx.x >= P.near_ctas;
+    // column mode: once every column of a tile CTA is finished, its warps take chunk tasks with the
+    // chunk CTAs (P.col_join): the left columns finish first, while the middle diagonals' chunk work is
+    // at its largest.  The CTA is finished when the last tile of its rightmost column, (0, Jr), is
+    // published: that tile waited for (0, Jr-1), read from the neighbour's shared buffers, and so on
+    // down the CTA's columns, so no warp of the CTA reads another's shared memory any more.
+    bool joined = false;
+    auto join_chunks = [&](int Jr) -> bool {
+        return Jr < 0 || warp_wait_geq(P.flags + P.seqs[0].flag_off + Jr, 1, P, lane);
+    };
     if constexpr (kHelp) {
         if (P.col_mode && P.col_helpers && split && !far_role) {
             // column mode with helpers: warp w < kHalf computes the rows of tile column J, warp
@@ -1694,97 +1703,117 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
             const int col_ctas = (NT + cpc - 1) / cpc;
             const bool main_role = warp < kHalf;
             const int w = main_role ? warp : warp - kHalf;
-            const int J = (col_ctas - 1 - (int)blockIdx.x) * cpc + w;
-            if ((int)blockIdx.x >= col_ctas || w >= cpc || cpc > kHalf || J >= NT) return;
-            ColHelp<Q> &ha = *reinterpret_cast<ColHelp<Q> *>(&wsb[w + kHalf]);
-            const bool consumer = (w + 1 < cpc) && (J + 1 < NT);
-            if (main_role) {
-                ColMain<Q> cs;
+            const int base = (col_ctas - 1 - (int)blockIdx.x) * cpc;
+            const int J = base + w;
+            const int ncols = ((int)blockIdx.x < col_ctas && cpc <= kHalf) ? max(0, min(cpc, NT - base)) : 0;
+            bool ok = true;
+            if (w < ncols) {
+                ColHelp<Q> &ha = *reinterpret_cast<ColHelp<Q> *>(&wsb[w + kHalf]);
+                const bool consumer = (w + 1 < cpc) && (J + 1 < NT);
+                if (main_role) {
+                    ColMain<Q> cs;
 #pragma unroll
-                for (int mm = 0; mm < 16; ++mm) cs.Wp[mm] = 0u;
-                cs.colT = 0;
-                cs.consumer = consumer;
-                for (int k = 0; k <= J; ++k) {
-                    const int I = J - k;
-                    const int idx = k * NT - k * (k - 1) / 2 + I;
-                    long long t0 = 0, tt[2] = {0, 0};
-                    if (P.trace && lane == 0) t0 = (long long)gtimer();
-                    const int nfar = k >= 1 ? P.tasks[idx].z : 0;
-                    const bool ok = col_main_tile<Q, MEMO>(P, sd, I, J, k, nfar, wsb[w], ha, Rs, lane, cs,
-                                                           P.trace ? tt : nullptr);
-                    if (P.trace && lane == 0 && ok) {
-                        long long *rec = P.trace + (size_t)idx * kTraceWords;
-                        rec[0] = ((long long)(blockIdx.x * kWarpsPerCta + warp) << 32) | (unsigned)idx;
-                        rec[1] = ((long long)kTaskNear << 32) | 0u;
-                        rec[2] = ((long long)I << 32) | (unsigned)J;
-                        rec[3] = t0;
-                        rec[4] = tt[0];
-                        rec[5] = tt[0];
-                        rec[6] = (long long)gtimer();
-                        rec[7] = tt[0];
-                        rec[8] = tt[1];
-                        rec[9] = tt[1];
-                        rec[10] = (long long)smid();
+                    for (int mm = 0; mm < 16; ++mm) cs.Wp[mm] = 0u;
+                    cs.colT = 0;
+                    cs.consumer = consumer;
+                    for (int k = 0; k <= J; ++k) {
+                        const int I = J - k;
+                        const int idx = k * NT - k * (k - 1) / 2 + I;
+                        long long t0 = 0, tt[2] = {0, 0};
+                        if (P.trace && lane == 0) t0 = (long long)gtimer();
+                        const int nfar = k >= 1 ? P.tasks[idx].z : 0;
+                        const bool tok = col_main_tile<Q, MEMO>(P, sd, I, J, k, nfar, wsb[w], ha, Rs, lane, cs,
+                                                                P.trace ? tt : nullptr);
+                        if (P.trace && lane == 0 && tok) {
+                            long long *rec = P.trace + (size_t)idx * kTraceWords;
+                            rec[0] = ((long long)(blockIdx.x * kWarpsPerCta + warp) << 32) | (unsigned)idx;
+                            rec[1] = ((long long)kTaskNear << 32) | 0u;
+                            rec[2] = ((long long)I << 32) | (unsigned)J;
+                            rec[3] = t0;
+                            rec[4] = tt[0];
+                            rec[5] = tt[0];
+                            rec[6] = (long long)gtimer();
+                            rec[7] = tt[0];
+                            rec[8] = tt[1];
+                            rec[9] = tt[1];
+                            rec[10] = (long long)smid();
+                        }
+                        if (!tok) {
+                            ok = false;
+                            break;
+                        }
                     }
-                    if (!ok) break;
+                } else {
+                    ColHelper<Q> hs;
+                    hs.have_lcb0 = false;
+                    hs.sj = lane < Cfg<Q, M>::T ? (int)P.codes[sd.code_off + J * Cfg<Q, M>::T + lane] : kPadCode;
+                    WarpScratch<Q, M> *prodM = w > 0 ? &wsb[w - 1] : nullptr;
+                    ColHelp<Q> *prodH = w > 0 ? reinterpret_cast<ColHelp<Q> *>(&wsb[w - 1 + kHalf]) : nullptr;
+                    for (int k = 0; k <= J; ++k)
+                        if (!col_help_prep<Q, MEMO>(P, sd, J - k, J, k, wsb[w], ha, prodM, prodH, Rs, lane, hs)) {
+                            ok = false;
+                            break;
+                        }
                 }
-            } else {
-                ColHelper<Q> hs;
-                hs.have_lcb0 = false;
-                hs.sj = lane < Cfg<Q, M>::T ? (int)P.codes[sd.code_off + J * Cfg<Q, M>::T + lane] : kPadCode;
-                WarpScratch<Q, M> *prodM = w > 0 ? &wsb[w - 1] : nullptr;
-                ColHelp<Q> *prodH = w > 0 ? reinterpret_cast<ColHelp<Q> *>(&wsb[w - 1 + kHalf]) : nullptr;
-                for (int k = 0; k <= J; ++k)
-                    if (!col_help_prep<Q, MEMO>(P, sd, J - k, J, k, wsb[w], ha, prodM, prodH, Rs, lane, hs)) break;
             }
-            return;
+            if (!P.col_join || !ok || (int)blockIdx.x >= col_ctas) return;
+            if (!join_chunks(base + ncols - 1)) return;
+            joined = true;
         }
     }
-    if (P.col_mode && split && !far_role) {
+    if (P.col_mode && split && !far_role && !joined) {
         // column mode: this warp computes the tiles of one column, bottom-up
         const SeqDesc sd = P.seqs[0];
         const int NT = sd.NT;
         // the longest columns (the right end, whose chains set the fold's time) go to the CTAs
         // launched first, away from the chunk CTAs that follow the tile CTAs in launch order
         const int col_ctas = (NT + P.cols_per_cta - 1) / P.cols_per_cta;
-        const int J = (col_ctas - 1 - (int)blockIdx.x) * P.cols_per_cta + warp;
-        if ((int)blockIdx.x >= col_ctas || warp >= P.cols_per_cta || J >= NT) return;
-        NearCol<Q, M> cs;
-        cs.prod = warp > 0 ? &wsb[warp - 1] : nullptr;
-        cs.consumer = (warp + 1 < P.cols_per_cta) && (J + 1 < NT);
-        cs.colT = 0;
-        cs.cnt_ok = false;
-        cs.tasks = P.tasks;
-        for (int k = 0; k <= J; ++k) {
-            const int I = J - k;
-            cs.k = k;
-            const int idx = k * NT - k * (k - 1) / 2 + I;   // tile (I,J) in the diagonal-ordered tile tasks
-            const int4 tk = P.tasks[idx];
-            long long t0 = 0, tdeps[4] = {0, 0, 0, 0};
-            if (P.trace && lane == 0) t0 = (long long)gtimer();
-            const long long tmid = run_near<Q, M, true, MEMO>(P, sd, I, J, tk.z, ws, Rs, lane, tdeps, cs);
-            if (P.trace && lane == 0) {
-                long long *rec = P.trace + (size_t)idx * kTraceWords;
-                rec[0] = ((long long)(blockIdx.x * kWarpsPerCta + warp) << 32) | (unsigned)idx;
-                rec[1] = ((long long)kTaskNear << 32) | (unsigned)tk.x;
-                rec[2] = ((long long)I << 32) | (unsigned)J;
-                rec[3] = t0;
-                rec[4] = tdeps[0];
-                rec[5] = tmid;
-                rec[6] = (long long)gtimer();
-                rec[7] = tdeps[1];
-                rec[8] = tdeps[2];
-                rec[9] = tdeps[3];
-                rec[10] = (long long)smid();
+        const int base = (col_ctas - 1 - (int)blockIdx.x) * P.cols_per_cta;
+        const int J = base + warp;
+        const int ncols = (int)blockIdx.x < col_ctas ? max(0, min(P.cols_per_cta, NT - base)) : 0;
+        bool failed = false;
+        if (warp < ncols) {
+            NearCol<Q, M> cs;
+            cs.prod = warp > 0 ? &wsb[warp - 1] : nullptr;
+            cs.consumer = (warp + 1 < P.cols_per_cta) && (J + 1 < NT);
+            cs.colT = 0;
+            cs.cnt_ok = false;
+            cs.tasks = P.tasks;
+            for (int k = 0; k <= J; ++k) {
+                const int I = J - k;
+                cs.k = k;
+                const int idx = k * NT - k * (k - 1) / 2 + I;   // tile (I,J) in the diagonal-ordered tile tasks
+                const int4 tk = P.tasks[idx];
+                long long t0 = 0, tdeps[4] = {0, 0, 0, 0};
+                if (P.trace && lane == 0) t0 = (long long)gtimer();
+                const long long tmid = run_near<Q, M, true, MEMO>(P, sd, I, J, tk.z, ws, Rs, lane, tdeps, cs);
+                if (P.trace && lane == 0) {
+                    long long *rec = P.trace + (size_t)idx * kTraceWords;
+                    rec[0] = ((long long)(blockIdx.x * kWarpsPerCta + warp) << 32) | (unsigned)idx;
+                    rec[1] = ((long long)kTaskNear << 32) | (unsigned)tk.x;
+                    rec[2] = ((long long)I << 32) | (unsigned)J;
+                    rec[3] = t0;
+                    rec[4] = tdeps[0];
+                    rec[5] = tmid;
+                    rec[6] = (long long)gtimer();
+                    rec[7] = tdeps[1];
+                    rec[8] = tdeps[2];
+                    rec[9] = tdeps[3];
+                    rec[10] = (long long)smid();
+                }
+                if (cs.failed) break;   // a wait gave up (its error is in P.error)
             }
-            if (cs.failed) break;   // a wait gave up (its error is in P.error)
+            failed = cs.failed;
         }
-        return;
+        if (!P.col_join || failed || (int)blockIdx.x >= col_ctas) return;
+        if (!join_chunks(base + ncols - 1)) return;
+        joined = true;
     }
+    const bool chunk_role = far_role || joined;
     NextTask nt;
-    nt.qhead = far_role ? P.queue_head_far : P.queue_head;
-    nt.qbase = far_role ? P.nnear : 0;
-    nt.qlimit = P.ring_cap > 0 ? 0x7fffffff : ((split && !far_role) ? P.nnear : P.ntasks);
+    nt.qhead = chunk_role ? P.queue_head_far : P.queue_head;
+    nt.qbase = chunk_role ? P.nnear : 0;
+    nt.qlimit = P.ring_cap > 0 ? 0x7fffffff : ((split && !chunk_role) ? P.nnear : P.ntasks);
     nt.tasks = P.tasks;
     nt.have = false;
     nt.stopped = false;

@@ -624,6 +624,7 @@ static void serve_loop(ServeState *S) {
                     p.col_mode = sp.col_mode;
                     p.cols_per_cta = sp.cpc;
                     p.col_helpers = sp.helpers;
+                    p.col_join = sp.join;
                     p.nnear = nnear;
                     p.near_ctas = sp.near_ctas;
                 }

@@ -88,3 +88,26 @@ def test_helper_option_range():
             f.option(fold.FOLD_OPT_COL_HELPERS, 2)
     finally:
         f.close()
+
+
+@pytest.mark.parametrize("join", [0, 1])
+@pytest.mark.parametrize("helpers", [0, 1])
+def test_finished_columns_join_chunks(join, helpers):
+    """Tile CTAs whose columns are all finished take chunk tasks (FOLD_OPT_COL_JOIN), with and without
+    helpers, 2 and 4 columns per tile CTA and the plain kernel: every table equals the oracle's."""
+    n = 61 * 32 + 9
+    seq = synth.structured(n, 4400 + join)
+    ref = oracle.nussinov(seq)
+    for method in ["two_vector", "plain"]:
+        f = fold.Folder(q=8, method=method)
+        try:
+            f.option(fold.FOLD_OPT_COL_JOIN, join)
+            assert f.option(fold.FOLD_OPT_COL_JOIN) == join
+            for cpc in [4, 2]:
+                if method == "plain" and helpers:
+                    continue
+                mp, D = _fold(f, seq, (62 + cpc - 1) // cpc, cpc, helpers)
+                assert mp == int(ref[0, n - 1])
+                assert np.array_equal(D.astype(np.int32), ref), (method, cpc, helpers, join)
+        finally:
+            f.close()
