@@ -191,9 +191,12 @@ SplitPlan plan_split(fold_ctx *ctx, const FoldOpts &o, int NT, int grid, bool la
     const double n = (double)NT * tile_of(ctx->q, ctx->method);
     const double work_ms = (148.0 / std::max(1, ctx->sm_count)) *
                            (ctx->method == kTwoVector ? n * n * n / (6.0 * ctx->q) / 4.3e9 : n * n * n / 6.0 / 1.77e10);
-    // chunk-only SMs get through their work ~1/0.86 faster than SMs that also run tiles (measured)
-    auto model = [&](double step_us, int near) {
-        return std::max(NT * step_us * 1e-3, work_ms * grid / std::max(1, grid - near) * (near > 0 ? 0.86 : 1.0));
+    // chunk-only SMs get through their work ~1/0.86 faster than SMs that also run tiles (measured);
+    // column CTAs that join the chunk workers when their columns end (the rightmost column of a CTA
+    // ends after a fraction of the fold proportional to its index) count as chunk SMs half the time
+    auto model = [&](double step_us, int near, bool joins = false) {
+        const double held = joins ? 0.5 * near : (double)near;
+        return std::max(NT * step_us * 1e-3, work_ms * grid / std::max(1.0, grid - held) * (near > 0 ? 0.86 : 1.0));
     };
     // tile-diagonal step of each layout (q = 8, measured on B300; with these figures both kernels
     // picked the fastest layout, or one within 1 %, at every size swept from n = 2000 to 16384)
@@ -211,14 +214,15 @@ SplitPlan plan_split(fold_ctx *ctx, const FoldOpts &o, int NT, int grid, bool la
     for (int k = 0; k < 2; ++k) {
         const int near = ceil_div(NT, cands[k]);
         if (near > grid / 3) continue;
-        const double m = model(step_col[k], near);
+        const int helpers = (help_ok && cands[k] <= kWarpsPerCta / 2) ? 1 : 0;
+        const double m = model(step_col[k], near, join_for(helpers) != 0);
         if (m < best) {
             best = m;
             sp.near_ctas = near;
             sp.col_mode = 1;
             sp.cpc = cands[k];
-            sp.helpers = (help_ok && cands[k] <= kWarpsPerCta / 2) ? 1 : 0;
-            sp.join = join_for(sp.helpers);
+            sp.helpers = helpers;
+            sp.join = join_for(helpers);
         }
     }
     return sp;
