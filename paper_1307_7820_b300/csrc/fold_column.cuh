@@ -333,8 +333,10 @@ __device__ __forceinline__ bool col_main_tile(const FoldParams &P, const SeqDesc
     if (lane == 0) st_release_cta(&ha.mprog, ms_base + G + 1);
     // the tile's row features (one ballot per row; horizontal vectors, Section 3.1), its P slot
     // cleared for tile (I, J+kRing) (the helper read it before publishing this tile's prep), and its
-    // release: this warp's fence covers its own global stores of the tile
-    {
+    // release: this warp's fence covers its own global stores of the tile.  The row features are
+    // read only by later tiles of row I, so not in the last column (the critical chain); the slot
+    // only if a tile (I, J+kRing) exists
+    if (J + 1 < NT) {
         bool up[T];
         int av[T];
 #pragma unroll
@@ -352,7 +354,9 @@ __device__ __forceinline__ bool col_main_tile(const FoldParams &P, const SeqDesc
             for (int r = 0; r < T; ++r)
                 rf_tile[(size_t)r * (Np / Q) + c] = ((uint32_t)av[r] << 16) | ((hb[r] >> (c * Q + 1)) & C::BMASK);
         }
-        if (nfar > 0) {
+    }
+    {
+        if (nfar > 0 && J + kRing < NT) {
             int *slot = P.pring + sd.p_off + ((size_t)(t % kRing) * NT + I) * (T * T);
             if constexpr ((T * T) % 4 == 0) {
 #pragma unroll

@@ -1321,7 +1321,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
 #pragma unroll
         for (int r = 0; r < T; ++r) ws.pm[r][c] = (int16_t)acc[r];
     }
-    if (nfar > 0) {   // ring slot reused by tile (I, J+kRing)
+    if (nfar > 0 && J + kRing < NT) {   // ring slot reused by tile (I, J+kRing)
         if constexpr (PBC) {
 #pragma unroll
             for (int k = lane; k < T * T / 4; k += 32) __stcg(reinterpret_cast<int4 *>(slot) + k, make_int4(0, 0, 0, 0));
@@ -1541,7 +1541,10 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
     if constexpr (COL) {
         if (lane == 0 && nn_next > 0) cnt_next = ld_relaxed(P.cnt + sd.cnt_off + (I - 1) * NT + J);
     }
+    // the row features of (I,J) are read by the middle blocks K = J of later tiles (I, J' > J) only:
+    // none in the last tile column, which is the fold's critical chain
     if constexpr (TV) {
+      if (J + 1 < NT) {
         bool up[T];
         int av[T];
 #pragma unroll
@@ -1564,6 +1567,7 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
                 }
             }
         }
+      }
     }
     if constexpr (COL) {
         // the tile (and its row features) is complete in shared memory: hand it to the next column's
