@@ -1693,9 +1693,26 @@ __global__ void __launch_bounds__(kThreads, 1) fold_kernel(FoldParams P) {
     // at its largest.  The CTA is finished when the last tile of its rightmost column, (0, Jr), is
     // published: that tile waited for (0, Jr-1), read from the neighbour's shared buffers, and so on
     // down the CTA's columns, so no warp of the CTA reads another's shared memory any more.
+    // The wait may last nearly the whole fold (the first tile CTA holds the last column), so it is
+    // not an error when it outlasts the wait bound: the warp then just leaves without joining.
     bool joined = false;
     auto join_chunks = [&](int Jr) -> bool {
-        return Jr < 0 || warp_wait_geq(P.flags + P.seqs[0].flag_off + Jr, 1, P, lane);
+        if (Jr < 0) return true;
+        const int *flag = P.flags + P.seqs[0].flag_off + Jr;
+        int ok = 0;
+        if (lane == 0) {
+            const unsigned long long t0 = gtimer();
+            unsigned ns = 64;
+            for (;;) {
+                if (ld_acquire(flag) >= 1) { ok = 1; break; }
+                if (*(volatile int *)P.error != 0 || (long long)(gtimer() - t0) > P.timeout_ns) break;
+                __nanosleep(ns);
+                ns = ns < 1024 ? 2 * ns : 1024;
+            }
+        }
+        ok = __shfl_sync(FULL, ok, 0);
+        __syncwarp();
+        return ok != 0;
     };
     if constexpr (kHelp) {
         if (P.col_mode && P.col_helpers && split && !far_role) {

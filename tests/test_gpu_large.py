@@ -179,3 +179,20 @@ def test_layouts_full_tables_repeated():
                     assert np.array_equal(D.astype(np.int32), ref)
             finally:
                 f.close()
+
+
+def test_column_mode_joining_with_short_wait_bound():
+    """n = 16384 in column mode with 8 columns per tile CTA, the tile CTAs joining the chunk workers,
+    and a 10 ms bound on every device wait: the first tile CTA's idle warps wait for its last column
+    about as long as the whole fold (~24 ms) and must leave quietly, not fail the fold; the table
+    equals the oracle's digest."""
+    seq = synth.variant("uniform", 16384, 16384)
+    f = fold.Folder(q=8)
+    try:
+        f.option(fold.FOLD_OPT_COLUMNS, 8)
+        f.option(fold.FOLD_OPT_COL_JOIN, 1)
+        f.option(fold.FOLD_OPT_TIMEOUT_MS, 10)
+        mp, D = f.score(seq, want_D=True)
+        _digest_check(D, seq, "uniform", 16384, "two-vector, column mode, joining")
+    finally:
+        f.close()
