@@ -1577,10 +1577,15 @@ __device__ __forceinline__ long long run_near(const FoldParams &P, const SeqDesc
             if (lane == 0) st_release_cta(&ws.produced, cs.k + 1);
         }
     }
-    // ---- column-major copy (lane = row); two-vector column mode reads columns only as features
+    // ---- column-major copy (lane = row); two-vector column mode reads columns only as features, and
+    // the other two-vector tiles read one column of it: the left neighbour's last, D(i, JT-1)
     if (lane < T && !(COL && TV)) {
+        if constexpr (TV) {
+            Dcol[(size_t)(JT + T - 1) * PC + IT + lane + kColOff] = tile[lane][T - 1];
+        } else {
 #pragma unroll 8
-        for (int cc = 0; cc < T; ++cc) Dcol[(size_t)(JT + cc) * PC + IT + lane + kColOff] = tile[lane][cc];
+            for (int cc = 0; cc < T; ++cc) Dcol[(size_t)(JT + cc) * PC + IT + lane + kColOff] = tile[lane][cc];
+        }
     }
     // answer D(0, n-1); on the serving ring it goes to host memory, after a system-scope fence that
     // makes the table (this warp's rows, and the other tiles it acquired) visible to the host's copies
