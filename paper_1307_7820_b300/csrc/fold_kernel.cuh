@@ -52,6 +52,10 @@ static __device__ __forceinline__ int ld_relaxed(const int *p) {
     return v;
 }
 static __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+// relaxed gpu-scope add without a return value (a release when a fence.acq_rel precedes it)
+static __device__ __forceinline__ void red_add(int *p, int v) {
+    asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 static __device__ __forceinline__ void st_relaxed(int *p, int v) {
     asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -630,8 +634,8 @@ __device__ __forceinline__ long long run_far(const FoldParams &P, const SeqDesc 
         if (lane == 0) {
             bulk_wait_all();
             fence_proxy_async_global();
-            __threadfence();
-            atomicAdd(P.cnt + sd.cnt_off + I * NT + J, 1);
+            fence_acq_rel();   // releases the merge with the relaxed count below
+            red_add(P.cnt + sd.cnt_off + I * NT + J, 1);
         }
         __syncwarp();
     } else {
@@ -816,8 +820,8 @@ __device__ __forceinline__ void merge_strip_bulk(const FoldParams &P, const SeqD
     if (lane == 0) {
         bulk_wait_all();
         fence_proxy_async_global();
-        __threadfence();
-        for (int s2 = 0; s2 < Seff; ++s2) atomicAdd(P.cnt + sd.cnt_off + I * NT + J0 + s2, 1);
+        fence_acq_rel();   // releases the merges with the relaxed counts below
+        for (int s2 = 0; s2 < Seff; ++s2) red_add(P.cnt + sd.cnt_off + I * NT + J0 + s2, 1);
     }
     __syncwarp();
 }
