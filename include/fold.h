@@ -119,10 +119,19 @@ enum fold_option {
                                   by round); 0 = repeated launches, each a slice of tile diagonals of
                                   every request.  Set before fold_serve_start (FOLD_EAGAIN while
                                   serving).  Results are identical. */
-    FOLD_OPT_COL_JOIN = 19     /* single folds in column mode: -1 = automatic (on without column
+    FOLD_OPT_COL_JOIN = 19,    /* single folds in column mode: -1 = automatic (on without column
                                   helpers), 1 = on, 0 = off.  On, the warps of a tile CTA whose tile
                                   columns are all finished take chunk tasks beside the chunk CTAs.
                                   Results are identical. */
+    FOLD_OPT_SERVE_LONG_TILES = 20, /* serving: a request of at least this many tiles per side (32
+                                  bases each) is long; default 160 (n >= 5089) */
+    FOLD_OPT_SERVE_LONG_CAP = 21 /* serving: at most this many long requests in flight at once
+                                  (default 2; 0 = no cap).  A long request beyond the cap waits, in
+                                  arrival order among long ones, while shorter requests behind it
+                                  are admitted past it (requests in flight share the device, so each
+                                  long one admitted slows the others).  Both set before
+                                  fold_serve_start (FOLD_EAGAIN while serving).  Results are
+                                  identical. */
 };
 
 /* One record per task of the last traced persistent launch. */

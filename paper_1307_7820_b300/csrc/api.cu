@@ -761,6 +761,16 @@ int fold_set_option(fold_ctx *ctx, int option, int64_t value) {
             if (ctx->serve) return FOLD_EAGAIN;
             ctx->serve_ring = (int)value;
             return FOLD_OK;
+        case FOLD_OPT_SERVE_LONG_TILES:
+            if (value < 1 || value > FOLD_MAX_N) return FOLD_EINVAL;
+            if (ctx->serve) return FOLD_EAGAIN;
+            ctx->serve_long_tiles = (int)value;
+            return FOLD_OK;
+        case FOLD_OPT_SERVE_LONG_CAP:
+            if (value < 0 || value > (1 << 20)) return FOLD_EINVAL;
+            if (ctx->serve) return FOLD_EAGAIN;
+            ctx->serve_long_cap = (int)value;
+            return FOLD_OK;
         case FOLD_OPT_BATCH_FLAT:
             if (value < -1 || value > 1) return FOLD_EINVAL;
             ctx->batch_flat_opt = (int)value;
@@ -796,6 +806,8 @@ int fold_get_option(fold_ctx *ctx, int option, int64_t *value) {
         case FOLD_OPT_COL_HELPERS: *value = ctx->col_helpers_opt; return FOLD_OK;
         case FOLD_OPT_COL_JOIN: *value = ctx->col_join_opt; return FOLD_OK;
         case FOLD_OPT_SERVE_RING: *value = ctx->serve_ring; return FOLD_OK;
+        case FOLD_OPT_SERVE_LONG_TILES: *value = ctx->serve_long_tiles; return FOLD_OK;
+        case FOLD_OPT_SERVE_LONG_CAP: *value = ctx->serve_long_cap; return FOLD_OK;
         case FOLD_OPT_BATCH_FLAT: *value = ctx->batch_flat_opt; return FOLD_OK;
         case FOLD_OPT_R_MEMO: *value = ctx->r_memo; return FOLD_OK;
         case FOLD_OPT_BATCH_GATHER: *value = ctx->batch_gather; return FOLD_OK;

@@ -80,6 +80,8 @@ struct fold_ctx {
     int col_helpers_opt = -1;  // FOLD_OPT_COL_HELPERS: -1 automatic, 0 off, 1 on (column mode, two-vector)
     int col_join_opt = -1;     // FOLD_OPT_COL_JOIN: -1 automatic (without helpers), 0 off, 1 on
     int serve_ring = 1;        // FOLD_OPT_SERVE_RING: serving through one persistent launch fed while it runs
+    int serve_long_tiles = 160;   // FOLD_OPT_SERVE_LONG_TILES: a request this many tiles per side is long
+    int serve_long_cap = 2;       // FOLD_OPT_SERVE_LONG_CAP: long requests in flight at once (0: no cap)
     int batch_flat_opt = -1;   // fold_batch chunks: -1 / 1 kc blocks each, 0 geometric sizes
     int batch_gather = 1;      // FOLD_OPT_BATCH_GATHER: fold_batch's list gathered on the device
     int r_memo = 0;            // FOLD_OPT_R_MEMO: tabulate R rows on first sight (two-vector, q <= 9)

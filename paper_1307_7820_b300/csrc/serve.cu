@@ -52,6 +52,7 @@ constexpr int kRingCap = 1 << 22;    // serving ring: tasks (64 MiB)
 constexpr long long kRingAhead = 8192;   // tasks published ahead of the claims the launch reported
 constexpr int kResultPending = INT32_MIN;
 constexpr size_t kSoloListBytes = size_t(256) << 20;   // device copies of lone requests' task lists
+constexpr size_t kAdmitScan = 256;   // queued requests looked at per admission pass
 
 struct Request {
     uint64_t ticket = 0;
@@ -109,6 +110,8 @@ struct ServeState {
     fold_ctx *ctx = nullptr;
     size_t budget = 0;
     int max_inflight = 0;
+    int long_tiles = 0;              // requests of at least this many tiles per side are long (0: none)
+    int long_cap = 0;                // ... and at most this many of them are in flight at once
     uint8_t *arena_base = nullptr;
     Arena arena;
     cudaStream_t st = nullptr;       // scheduler stream
@@ -554,16 +557,29 @@ static void serve_loop(ServeState *S) {
             if (S->inflight.empty() && S->queued.empty())
                 S->cv.wait_for(lk, std::chrono::milliseconds(50), [&] { return S->stop || !S->queued.empty(); });
             if (S->stop) return;
-            // admission: FIFO while the arena has room and the in-flight limit allows
-            while (!S->queued.empty() && (int)S->inflight.size() < S->max_inflight) {
-                Request &r = S->reqs[S->queued.front()];
+            // admission: in arrival order while the arena has room and the in-flight limit allows.
+            // Long requests (at least long_tiles tiles per side) beyond long_cap in flight wait, in
+            // their order, and shorter ones behind them are admitted past them: in flight, requests
+            // share the launch round by round, so every long one admitted slows the others.
+            int nlong = 0;
+            if (S->long_tiles > 0)
+                for (uint64_t t : S->inflight) nlong += S->reqs[t].NT >= S->long_tiles ? 1 : 0;
+            size_t qi = 0;
+            while (qi < S->queued.size() && qi < kAdmitScan && (int)S->inflight.size() < S->max_inflight) {
+                Request &r = S->reqs[S->queued[qi]];
+                const bool is_long = S->long_tiles > 0 && r.NT >= S->long_tiles;
+                if (is_long && nlong >= S->long_cap) {
+                    ++qi;
+                    continue;
+                }
                 size_t off;
-                if (!S->arena.alloc(r.bytes, &off)) break;
+                if (!S->arena.alloc(r.bytes, &off)) break;   // memory: no request passes another
                 r.block = off;
                 r.state = 1;
                 S->inflight.push_back(r.ticket);
                 admitted.push_back(r.ticket);
-                S->queued.pop_front();
+                S->queued.erase(S->queued.begin() + (std::ptrdiff_t)qi);
+                nlong += is_long ? 1 : 0;
             }
             for (uint64_t t : S->inflight) active.push_back(&S->reqs[t]);
         }
@@ -821,6 +837,8 @@ int fold_serve_start(fold_ctx *ctx, int64_t budget_bytes, int32_t max_inflight) 
     S->ctx = ctx;
     S->budget = (size_t)budget_bytes;
     S->max_inflight = max_inflight;
+    S->long_tiles = ctx->serve_long_cap > 0 ? ctx->serve_long_tiles : 0;
+    S->long_cap = ctx->serve_long_cap;
     S->near_ctas = ctx->near_ctas_opt > 0 ? ctx->near_ctas_opt : 0;
     if (cudaMalloc(&S->arena_base, S->budget) != cudaSuccess) {
         cudaGetLastError();

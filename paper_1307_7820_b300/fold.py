@@ -24,6 +24,8 @@ FOLD_OPT_TIMING, FOLD_OPT_KERNEL_NS, FOLD_OPT_TRACE, FOLD_OPT_NEAR_CTAS, FOLD_OP
 FOLD_OPT_BATCH_FLAT, FOLD_OPT_R_MEMO, FOLD_OPT_BATCH_GATHER = 14, 15, 16
 FOLD_OPT_COL_HELPERS = 17
 FOLD_OPT_SERVE_RING = 18
+FOLD_OPT_SERVE_LONG_TILES = 20
+FOLD_OPT_SERVE_LONG_CAP = 21
 FOLD_OPT_COL_JOIN = 19
 FOLD_PAIRS_DEFAULT = 0x5A48   # AU UA CG GC GU UG
 FOLD_PAIRS_PAPER = 0x1248     # AU UA CG GC

@@ -71,6 +71,35 @@ def test_serve_mix_equals_alone(ring):
         f.close()
 
 
+def test_serve_long_request_cap():
+    # requests of at least 20 tile columns (n >= 609) are long and at most one of them is in flight:
+    # the others wait in arrival order while the short ones pass them; every answer as the oracle's
+    f = fold.Folder(q=8)
+    try:
+        assert f.option(fold.FOLD_OPT_SERVE_LONG_TILES) == 160 and f.option(fold.FOLD_OPT_SERVE_LONG_CAP) == 2
+        for opt, bad in ((fold.FOLD_OPT_SERVE_LONG_TILES, 0), (fold.FOLD_OPT_SERVE_LONG_CAP, -1)):
+            with pytest.raises(fold.FoldError) as ei:
+                f.option(opt, bad)
+            assert ei.value.code == fold.FOLD_EINVAL
+        f.option(fold.FOLD_OPT_SERVE_LONG_TILES, 20)
+        f.option(fold.FOLD_OPT_SERVE_LONG_CAP, 1)
+        kinds = ["uniform", "gc_rich", "structured"]
+        lens = [900, 40, 1300, 75, 650, 120, 1100, 33, 700, 260, 610, 9]
+        seqs = [synth.variant(kinds[k % 3], L, 5100 + k) for k, L in enumerate(lens)]
+        fold.fold_serve_start(f.ctx, 8 << 30, 64)
+        with pytest.raises(fold.FoldError) as ei:
+            f.option(fold.FOLD_OPT_SERVE_LONG_CAP, 3)   # fixed while serving
+        assert ei.value.code == fold.FOLD_EAGAIN
+        tickets = [fold.fold_serve_submit(f.ctx, s) for s in seqs]
+        res = _drain(f.ctx, tickets)
+        assert [res[t] for t in tickets] == [oracle.score(s) for s in seqs]
+        st = fold.fold_serve_stats(f.ctx)
+        assert st["admitted"] == st["finished"] == len(seqs)
+    finally:
+        fold.fold_serve_stop(f.ctx)
+        f.close()
+
+
 def test_serve_lone_requests_fold_in_one_launch():
     # each request arrives to an idle server: up to 8192 long it folds in one launch with the single
     # fold's work split (stats "solo"), longer ones slice by slice; scores and tables as alone
