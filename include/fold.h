@@ -395,7 +395,9 @@ int fold_batch_dev_table(fold_ctx *ctx, const fold_batch_plan *plan, const void 
 /* Serving (continuous batching).  fold_serve_start starts a host scheduler
  * thread that admits submitted requests while the device memory their two
  * int16 D copies need (about 4*n^2 bytes each) fits `budget_bytes` and at
- * most `max_inflight` are in flight.  A request arriving to an idle server
+ * most `max_inflight` are in flight, of which at most FOLD_OPT_SERVE_LONG_CAP
+ * are long (FOLD_OPT_SERVE_LONG_TILES; shorter requests are admitted past a
+ * long one that waits for that cap).  A request arriving to an idle server
  * (n <= 8192) folds alone in one launch with the single fold's work split.
  * Otherwise the in-flight requests are folded by one persistent launch that
  * the thread feeds while it runs (FOLD_OPT_SERVE_RING, default): round after
