@@ -3,7 +3,10 @@
 // A host scheduler thread owns one device arena of `budget_bytes`.  Submitted
 // requests wait in a FIFO until their workspace (D copies, difference
 // vectors, tile flags: the single-sequence plan) fits the arena and fewer
-// than `max_inflight` requests are in flight.  A request arriving to an idle
+// than `max_inflight` requests are in flight; a long request (at least
+// FOLD_OPT_SERVE_LONG_TILES tiles per side) also waits while
+// FOLD_OPT_SERVE_LONG_CAP long ones are in flight, and shorter requests behind
+// it are admitted past it.  A request arriving to an idle
 // server (up to kSoloMaxN bases) folds alone in one launch with the single
 // fold's work split.  Otherwise the in-flight requests are folded by one
 // persistent launch fed while it runs (the serving ring): the thread
