@@ -29,6 +29,7 @@ FOLD_OPT_SERVE_LONG_CAP = 21
 FOLD_OPT_COL_JOIN = 19
 FOLD_PAIRS_DEFAULT = 0x5A48   # AU UA CG GC GU UG
 FOLD_PAIRS_PAPER = 0x1248     # AU UA CG GC
+FOLD_ABI_VERSION = 1
 FOLD_MAX_N = 65535
 FOLD_STATIC_MAX_N = 1024
 

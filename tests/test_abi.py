@@ -33,6 +33,25 @@ def test_every_declared_symbol_is_exported(L):
     assert sorted(fold.ABI_SYMBOLS) == names
 
 
+def test_option_and_status_constants_match_the_header():
+    # every FOLD_OPT_* / FOLD_* enumerator and #define of include/fold.h has the same value in the binding
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "fold.h")).read(), flags=re.S)
+    consts = {}
+    for body in re.findall(r"enum\s*\w*\s*\{(.*?)\}", src, flags=re.S):
+        nxt = 0
+        for item in [x.strip() for x in body.split(",") if x.strip()]:
+            name, _, val = item.partition("=")
+            nxt = int(val.strip(), 0) if val.strip() else nxt
+            consts[name.strip()] = nxt
+            nxt += 1
+    for name, val in re.findall(r"#define\s+(FOLD_[A-Z0-9_]+)\s+(0x[0-9A-Fa-f]+|\d+)", src):
+        consts[name] = int(val, 0)
+    opts = [k for k in consts if k.startswith("FOLD_OPT_")]
+    assert len(opts) >= 21
+    for name, val in consts.items():
+        assert getattr(fold, name) == val, name
+
+
 def test_strerror_all_codes(L):
     for code in range(7):
         s = fold.fold_strerror(code)
